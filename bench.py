@@ -1,0 +1,378 @@
+"""Benchmark: 3D DDI evaluations/s at 128^3 (FP32-mixed path, error vs the FP64 path),
+with the HBM roofline of the dominant kernel, an end-to-end host-buffer number and the
+FP64 CPU oracle timed on this machine's cores.
+
+Workload (one step = one DDI, i.e. one pass of the whole hot path: pad, 3 forward FFT
+passes, interpolation x symbol x weights, spread, 3 inverse FFT passes, crop): 128^3 grid
+on [-12,12)^3, density a seeded sum of 8 anisotropic Gaussians (widths U[0.5,2], centres
+U[-4,4]^3), dipole axis n = (sin 30, 0, cos 30), quadrature 128 x 64 x 128 (1,048,576
+nodes), NUFFT tolerance 1e-6.  Rank r of a multi-GPU run evaluates the density with seed
+r (independent densities, no exchange: weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 128
+L = 12.0
+SIZES = dict(nr=128, ntheta=64, nphi=128)
+METRIC = "3D DDI evals/s at 128^3 (FP32-mixed vs FP64, rel err <=1e-6); % of HBM roofline"
+UNIT = "DDI/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _workload_cfg(extra=None):
+    cfg = {"workload": "ddi3d_128cubed_mixture8_tilt30_quad128x64x128", "grid": [N, N, N], "box": [-L, L],
+           "quadrature": [SIZES["nr"], SIZES["ntheta"], SIZES["nphi"]], "nodes": N * 64 * 128,
+           "nufft_tol": 1e-6, "seed_per_rank": True, "l2": "flushed before every timed step (256 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(target_s=12.0, seed=0, max_nodes=None):
+    """FP64 oracle (direct nonuniform DFT) on a bounded node sample; returns DDI/s and detail.
+
+    The oracle's cost is linear in the node count (type 2: nodes x grid, type 1: nodes x
+    grid), so the time of a full DDI is the sample time scaled by M / sample nodes."""
+    import numpy as np
+    from oracle import nudft
+    from oracle import quadrature as qd
+    from paper_1504_02897_gb300 import synth
+    w = synth.gaussian_mixture_density(N, L, seed=seed)
+    t = qd.plan_tables(3, w["n"], w["len"], w["axis"], **SIZES)
+    M = t["k"].shape[0]
+    rng = np.random.default_rng(0)
+    s = 512
+    elapsed = 0.0
+    while True:
+        sel = rng.choice(M, s, replace=False)
+        k, W = t["k"][sel], t["W"][sel]
+        t0 = time.perf_counter()
+        rh = nudft.type2(w["rho"], k, w["n"], w["lo"], w["len"])
+        nudft.type1(W * rh, k, w["n"], w["lo"], w["len"])
+        elapsed = time.perf_counter() - t0
+        if elapsed >= target_s / 4 or (max_nodes and s >= max_nodes) or s >= M:
+            break
+        s = min(M, int(s * max(2.0, min(8.0, target_s / max(elapsed, 1e-3) / 2))))
+    full = elapsed * M / s
+    return 1.0 / full, {"sample_nodes": s, "sample_seconds": elapsed, "full_ddi_seconds_est": full}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import nudft
+    from oracle import quadrature as qd
+    from paper_1504_02897_gb300 import synth
+    w = synth.gaussian_mixture_density(N, L, seed=0)
+    t = qd.plan_tables(3, w["n"], w["len"], w["axis"], **SIZES)
+    M = t["k"].shape[0]
+    s = 1024
+    rng = np.random.default_rng(0)
+    times = []
+    for it in range(args.warmup + args.steps):
+        sel = rng.choice(M, s, replace=False)
+        k, W = t["k"][sel], t["W"][sel]
+        t0 = time.perf_counter()
+        rh = nudft.type2(w["rho"], k, w["n"], w["lo"], w["len"])
+        nudft.type1(W * rh, k, w["n"], w["lo"], w["len"])
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt * M / s)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    cores = os.cpu_count()
+    sample = f"{s} of {M} quadrature nodes per step (type 2 over the full 128^3 grid, type 1 onto it); " \
+             f"time scaled by M/{s}"
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": _workload_cfg({"engine": "FP64 CPU oracle (direct nonuniform DFT, numpy BLAS)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# algorithmic bytes per launch of each kernel (FP32-mixed path, nf = 2N), see the design doc
+def kernel_bytes(name, info, real=4):
+    cx = 2 * real
+    n3 = N ** 3
+    nf3 = (2 * N) ** 3
+    mh = int(info.nodes_used)
+    node_in = mh * (8 + 4 * real)          # ushort4 start taps + 4 reals (offsets, weight)
+    table = {
+        "pad": n3 * real + nf3 * cx,
+        "fft_x_fwd": 2 * nf3 * cx, "fft_y_fwd": 2 * nf3 * cx, "fft_z_fwd": 2 * nf3 * cx,
+        "fft_x_inv": 2 * nf3 * cx, "fft_y_inv": 2 * nf3 * cx, "fft_z_inv": 2 * nf3 * cx,
+        "interp": nf3 * cx + node_in + mh * cx,
+        "spread": nf3 * cx + node_in + mh * cx,
+        "spread_reduce": 0,
+        "crop": n3 * cx + n3 * real,
+    }
+    return table.get(name, 0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1504_02897_gb300 import build, ddi, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    ddi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    w = synth.gaussian_mixture_density(N, L, seed=rank)
+    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP32, **SIZES)
+    rho = torch.from_numpy(w["rho"]).to(dev, torch.float32)
+    phi = torch.empty_like(rho)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # accuracy of the timed FP32 path against the FP64 GPU path (itself parity-tested
+    # against the FP64 oracle to 1e-12)
+    plan64 = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP64, **SIZES)
+    rho64 = torch.from_numpy(w["rho"]).to(dev)
+    phi64 = plan64.apply(rho64)
+    plan.apply(rho, phi)
+    torch.cuda.synchronize()
+    err32 = float((phi.double() - phi64).abs().max() / phi64.abs().max())
+    # FP64 path throughput (a few steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    t64 = []
+    for i in range(4):
+        flush.fill_(float(i))
+        ev[0].record(stream)
+        plan64.apply(rho64, phi64)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            t64.append(ev[0].elapsed_time(ev[1]))
+    del plan64, rho64, phi64
+    torch.cuda.empty_cache()
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        plan.apply(rho, phi)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))           # L2 flush: 256 MiB write between timed steps
+        starts[i].record(stream)
+        plan.apply(rho, phi)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1e3
+    t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    total_ddi = args.steps * world
+    value = total_ddi / tmax
+    ms_per_step = tmax / args.steps * 1e3
+
+    # per-kernel CUDA-event times (same stream, L2 flushed before each call)
+    per = {}
+    launches = 0
+    for i in range(8):
+        flush.fill_(float(i))
+        _, marks = plan.apply_timed(rho, phi)
+        launches = len(marks)
+        if i < 2:
+            continue
+        for name, ms in marks:
+            per.setdefault(name, []).append(ms)
+    avg = {k: sum(v) / len(v) for k, v in per.items()}
+    dominant = max(avg, key=avg.get)
+    peaks, src = _peaks()
+    peak = float(peaks["hbm_gbs"])
+    info = plan.info
+    alg = kernel_bytes(dominant, info)
+    achieved = alg / (avg[dominant] * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic_ddi3d_128.json")
+    if os.path.exists(prof):
+        try:
+            tr = json.load(open(prof))
+            if tr.get("kernel") == dominant and tr.get("source_hash") == _kernel_hash():
+                traffic = tr.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    ddi_bytes = 8 * N ** 3 + 2 * 4 * (2 * N) ** 3 * 8
+
+    # end to end: pinned host buffers, H2D + DDI + D2H inside the timed region
+    host_in = torch.from_numpy(w["rho"].astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(2):
+        plan.apply_host(host_in, host_out)
+    e2e_steps = max(5, args.steps // 2)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        plan.apply_host(host_in, host_out)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = e2e_steps * world / float(te.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, detail = cpu_oracle_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{detail['sample_nodes']} of {N * 64 * 128} nodes (type 2 + type 1 over the full 128^3 "
+                         f"grid) in {detail['sample_seconds']:.1f} s, scaled by nodes"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _workload_cfg({"fp32_rel_err_vs_fp64": err32, "fp64_ddi_per_s": 1e3 / (sum(t64) / len(t64)),
+                                     "nufft_points_per_s": value * 2 * N * 64 * 128,
+                                     "kernel_width": info.width, "wall_s": wall}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dominant,
+                         "kernel_ms": avg[dominant], "peak_source": src + " hbm_gbs (copy)"},
+            "ddi_roofline": {"algorithmic_bytes": ddi_bytes, "achieved": ddi_bytes / (ms_per_step * 1e-3) / 1e9,
+                             "frac": ddi_bytes / (ms_per_step * 1e-3) / 1e9 / peak, "unit": "GB/s"},
+            "kernel_ms": avg,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N ** 3, "d2h_bytes_per_step": 4 * N ** 3},
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+        }
+        if cpu:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("fft.cu", "nufft.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1504_02897_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

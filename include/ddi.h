@@ -1,0 +1,186 @@
+/*
+ * ddi.h -- C ABI of the GB300 NUFFT dipole-dipole interaction (DDI) library.
+ *
+ * The library evaluates the dipolar potential Phi = U_dip * rho of a density rho given
+ * on a uniform grid (Sec. 1, Eqs. DipGPE0 / dipole-poten0 / DipKer; two axes: Eq. dipmn)
+ * by the NUFFT method of Sec. 2.1 (Eq. DDI-Trun1): a type-2 NUFFT takes rho to a
+ * spherical (3D) or polar (2D) Fourier quadrature, the values are multiplied by the
+ * symbol and the quadrature weights, and a type-1 NUFFT sums them back onto the grid.
+ * On top of it sit the time-splitting step (Sec. 4.1, Eq. tssp2, Case I), the
+ * energies of Sec. 3.2, the normalised gradient flow (Sec. 3.1, Eqs. gf-eq2..gffg33)
+ * and the adjoint of the time-splitting step.
+ *
+ * Conventions shared by every entry point
+ *  - Grids are C-ordered [z][y][x] (3D) or [y][x] (2D), x fastest; grid point
+ *    j = (jx, jy, jz) sits at x_j = lo + j * h with h_d = len_d / n_d (the periodic
+ *    duplicate endpoint of Sec. 4.1 is dropped).
+ *  - A plan has a precision: DDI_FP64 (real arrays double, complex arrays interleaved
+ *    double pairs) or DDI_FP32 (FP32 arrays and interleaved float pairs; quadrature
+ *    nodes, weights and deconvolution factors are built in FP64 and rounded once).
+ *  - "Device pointer" arguments must be device memory of the plan's device, laid out
+ *    as above, owned by the caller.  "Host pointer" arguments are host memory owned by
+ *    the caller (pinned memory is fastest).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry points that
+ *    only launch work return before it finishes; those that return scalars synchronise
+ *    the stream.
+ *  - Every entry point returns a ddi_status; no exception or abort crosses the ABI.
+ *    Arguments are validated before any launch; ddi_last_error() then describes the
+ *    failure (thread-local string, valid until the next call on that thread).
+ */
+#ifndef DDI_GB300_H
+#define DDI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDI_OK = 0,
+  DDI_ERR_ARG = -1,        /* invalid argument (sizes, axes, pointers, precision) */
+  DDI_ERR_CUDA = -2,       /* a CUDA runtime call or kernel launch failed */
+  DDI_ERR_OOM = -3,        /* device allocation failed in ddi_plan_create */
+  DDI_ERR_NONFINITE = -4,  /* NaN/Inf found in an input or produced by an iteration */
+  DDI_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+  DDI_ERR_NOCONV = -6      /* an iteration hit its step limit before the tolerance */
+} ddi_status;
+
+enum { DDI_FP64 = 0, DDI_FP32 = 1 };
+
+typedef struct ddi_plan_s* ddi_plan;
+
+/* Plan descriptor.  Zero fields take the defaults listed. */
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int n[3];            /* grid sizes (x, y, z); powers of two, 8..1024 (3D: <= 512); n[2] = 1 in 2D */
+  double lo[3];        /* lower box corner per axis */
+  double len[3];       /* box length per axis (> 0) */
+  double axis_n[3];    /* dipole axis n (unit vector; Eq. DipKer).  In 2D n_perp = (n0, n1), n3 = n2 */
+  double axis_m[3];    /* second axis m (Eq. dipmn); all zero => m = n */
+  int nr, ntheta, nphi;/* quadrature sizes; 0 => (N, N/2, N) in 3D, (2N, -, 2N) in 2D, N = max n */
+  double kmax;         /* radius R of the Fourier ball; 0 => pi / min_d h_d */
+  int precision;       /* DDI_FP64 or DDI_FP32 */
+  double nufft_tol;    /* requested NUFFT tolerance; 0 => 1e-13 (FP64) / 1e-6 (FP32) */
+  int tile[3];         /* spread tile (x, y, z) in fine cells; 0 => built-in choice */
+  int chunk;           /* max nodes per spread work item; 0 => built-in choice */
+} ddi_plan_desc;
+
+/* Read-only facts about a built plan (sizes and the NUFFT parameters chosen). */
+typedef struct {
+  int dim, precision;
+  int n[3];
+  int nf[3];           /* oversampled (fine) grid, 2 n per axis */
+  int width;           /* exponential-of-semicircle kernel width in fine cells */
+  double beta;         /* kernel shape parameter */
+  int64_t nodes;       /* quadrature nodes M (the full, antipodally closed set) */
+  int64_t nodes_used;  /* nodes processed per NUFFT (M/2: one of each +-k pair) */
+  int tile[3];
+  int spread_items, spread_split_tiles, interp_items;
+  double kmax;
+  int nr, ntheta, nphi;
+  size_t device_bytes; /* device memory held by the plan */
+} ddi_plan_info;
+
+/* Energies of Sec. 3.2 for a state phi (all FP64). */
+typedef struct {
+  double E, mu, Ekin, Epot, Eint, Edip, virial, mass;
+  int steps;           /* gpe_ground_state: outer steps taken */
+  int inner_max;       /* gpe_ground_state: largest inner iteration count of any step */
+  double last_change;  /* gpe_ground_state: |E^{n+1} - E^n| or max|phi^{n+1}-phi^n|/dt at exit */
+} gpe_stats;
+
+enum { GPE_STOP_ENERGY = 0, GPE_STOP_PAPER = 1 };
+
+/* ---- status ---------------------------------------------------------------- */
+const char* ddi_status_str(int status);   /* static string for a status code */
+const char* ddi_last_error(void);         /* detail of the last failure on this thread */
+
+/* ---- quadrature tables (host only, no GPU needed) --------------------------- */
+/* Sec. 2.1, Eq. DDI-Trun1: nodes k_q and weights W_q of the discrete sum
+ *   Phi_j = Re sum_q W_q e^{i k_q.x_j} h^d sum_j' rho_j' e^{-i k_q.x_j'}.
+ * Rule: n_r-point Gauss-Legendre radial on [0, R], n_theta-point Gauss-Legendre in
+ * cos(theta), n_phi-point trapezoid azimuth whose second half is the exact negation
+ * of the first; W_q = w_q |k|^{d-1} Uhat(k_q) / (2 pi)^d.  Node order
+ * q = (i_r n_theta + j_u) n_phi + m (3D), i_r n_phi + m (2D).
+ * k: [M][dim] doubles, W: [M] doubles, l0: [M][dim] int32 (first fine-grid tap,
+ * ceil(k_d h_d nf_d / (2 pi) - w/2), before wrapping), each may be NULL.  Call with
+ * all three NULL to get *M only.  Host pointers. */
+int ddi_quadrature_tables(const ddi_plan_desc* desc, int64_t* M, double* k, double* W,
+                          int32_t* l0);
+
+/* ---- plans ------------------------------------------------------------------ */
+/* Build a plan on the current device: quadrature, NUFFT tables, node binning, spread
+ * work list and all device workspace (fine grid, node arrays, GPE buffers).  The
+ * only call that allocates.  `stream` orders the table uploads. */
+int ddi_plan_create(ddi_plan* out, const ddi_plan_desc* desc, void* stream);
+int ddi_plan_destroy(ddi_plan plan);
+int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info);
+
+/* ---- the DDI (Sec. 2.1) -------------------------------------------------------- */
+/* Phi = U_dip * rho by the quadrature sum above, through the NUFFT: deconvolve and
+ * pad rho into the 2x oversampled grid, FFT, interpolate at one node of each +-k pair,
+ * multiply by 2 h^d W_q, spread, inverse FFT, crop, deconvolve, real part.
+ * rho, phi: device pointers to n-sized real grids in the plan precision; may alias. */
+int ddi_apply(ddi_plan plan, const void* rho, void* phi, void* stream);
+
+/* Same, end to end from host memory: copies rho in, applies, copies phi out, and
+ * synchronises `stream`.  rho_host / phi_host: host pointers (pinned recommended). */
+int ddi_apply_host(ddi_plan plan, const void* rho_host, void* phi_host, void* stream);
+
+/* ddi_apply with a CUDA event recorded on `stream` after every kernel launch; on
+ * return (the stream is synchronised) names[i] / ms[i] hold the i-th launch's kernel
+ * name (static string) and its duration in milliseconds, *count the number of launches
+ * (at most `cap`).  Same arguments and result as ddi_apply; used by benchmarks to time
+ * single kernels on the stream they run on. */
+int ddi_apply_timed(ddi_plan plan, const void* rho, void* phi, void* stream, const char** names, double* ms,
+                    int cap, int* count);
+
+/* Type-2 stage alone (for tests): f_q for the nodes in the plan's processing order,
+ * scaled as the path uses them, c_q = 2 h^d W_q f_q.  c: device pointer to
+ * nodes_used complex values; order: ddi_plan_node_order(). */
+int ddi_type2(ddi_plan plan, const void* rho, void* c, void* stream);
+/* Type-1 stage alone: phi_j = Re sum_q c_q e^{i k_q.x_j} (plan order, nodes_used). */
+int ddi_type1(ddi_plan plan, const void* c, void* phi, void* stream);
+/* Original node index q (0..M-1) of each processed node, host pointer [nodes_used]. */
+int ddi_plan_node_order(ddi_plan plan, int64_t* q);
+
+/* ---- GPE (Secs. 3-4) -------------------------------------------------------------- */
+/* nsteps Strang steps of Eq. tssp2, Case I (f = 0, sigma = 1, fixed axis):
+ * psi <- K N K psi with K = F^{-1} exp(-i dt |mu|^2/4) F and
+ * N: psi <- psi exp(-i dt (V + beta |psi|^2 + lambda Phi(|psi|^2))), Phi by ddi_apply.
+ * psi: device complex grid (in place); V: device real grid. */
+int gpe_step(ddi_plan plan, void* psi, const void* V, double beta, double lambda,
+             double dt, int nsteps, void* stream);
+
+/* Energies of Sec. 3.2 (E_kin spectral, FP64 reductions), mu = E + E_int + E_dip,
+ * virial I = 2E_kin - 2E_pot + 3E_int + 3E_dip (Eq. vir_iden), mass.  Synchronises. */
+int gpe_energy(ddi_plan plan, const void* psi, const void* V, double beta, double lambda,
+               gpe_stats* out, void* stream);
+
+/* Normalised gradient flow, backward Euler (Eqs. gf-eq2..gffg33); the implicit
+ * equation is solved by the stabilised fixed point
+ *   phi1 <- F^{-1}[F(phi/dt + (alpha - W) phi1) / (1/dt + alpha + |mu|^2/2)],
+ * W = V + beta|phi|^2 + lambda Phi, alpha = (max W + min W)/2, until
+ * max|change| <= inner_tol (or 200 sweeps), then phi <- phi1/||phi1||.
+ * Stops when rule = GPE_STOP_ENERGY: |E^{n+1} - E^n| < tol, GPE_STOP_PAPER:
+ * max|phi^{n+1}-phi^n|/dt <= tol (Sec. 3.2); checked every `check_every` steps.
+ * Returns DDI_ERR_NOCONV when max_steps is reached.  phi: device complex grid, in
+ * place (normalised on entry).  Synchronises. */
+int gpe_ground_state(ddi_plan plan, void* phi, const void* V, double beta, double lambda,
+                     double dt, double tol, int rule, double inner_tol, int max_steps,
+                     int check_every, gpe_stats* out, void* stream);
+
+/* Adjoint of one gpe_step step (nsteps = 1) for the pairing Re h^d sum conj(a) b.
+ * psi_in: the step's input state (device, read only; the step is recomputed);
+ * cot: device complex grid holding dJ/dpsi_out on entry, dJ/dpsi_in on exit;
+ * grad_V: device real grid, incremented by h^d r with r = Re(conj(-i dt psi2) g2)
+ * (the step's contribution to dJ/dV_j).  One DDI of r (Phi is self-adjoint). */
+int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V,
+                     const void* V, double beta, double lambda, double dt, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDI_GB300_H */

@@ -1,0 +1,167 @@
+// Shared device/host definitions of the DDI library: the plan object, complex helpers,
+// error reporting.  Included by every .cu translation unit of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ddi.h"
+#include "tables.h"
+
+namespace ddi {
+
+// ---- error reporting (thread-local message behind ddi_last_error) ----------------
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+#define DDI_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ::ddi::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                       __LINE__);                                                       \
+      return DDI_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+#define DDI_LAUNCH_CHECK()                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) {                                                            \
+      ::ddi::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),      \
+                       __FILE__, __LINE__);                                             \
+      return DDI_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+#define DDI_TRY(expr)          \
+  do {                         \
+    int s_ = (expr);           \
+    if (s_ != DDI_OK) return s_; \
+  } while (0)
+
+// ---- complex types -------------------------------------------------------------
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {
+  C r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+
+// ---- spread work list ------------------------------------------------------------
+struct SpreadItem {
+  int tile;   // linear tile index (tz * ntiles_y + ty) * ntiles_x + tx
+  int vbeg;   // range in the tile's visit list (its own bin and the lower neighbours)
+  int vend;
+  int slot;   // -1: write the tile to the fine grid; >= 0: write to partial slot
+};
+struct SplitTile {
+  int tile, slot0, nslots, pad;
+};
+
+// ---- the plan ----------------------------------------------------------------------
+struct Plan {
+  ddi_plan_desc desc{};
+  int dim = 3, prec = DDI_FP64;
+  int n[3] = {1, 1, 1};
+  int nf[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  double dv = 1.0;  // h_1 h_2 h_3
+  int w = 8;
+  double beta = 0.0;
+  int64_t M = 0, Mh = 0;
+  int tile[3] = {1, 1, 1};
+  int ntile[3] = {1, 1, 1};
+  int nbins = 0;
+  int chunk = 0;
+  int device = 0;
+  size_t bytes = 0;
+
+  QuadTables quad;                   // host copy of the tables (export, tests)
+  std::vector<int64_t> order;        // processing order -> original node index
+
+  // device arrays (element types depend on prec)
+  void* d_l0 = nullptr;       // ushort4 [Mh]: wrapped first tap (x, y, z)
+  void* d_pos = nullptr;      // T4 [Mh]: (fx, fy, fz, 2 h^d W_q), f = s - l0 - w/2
+  void* d_c = nullptr;        // cx [Mh]: node values between interp and spread
+  void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
+  void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
+  void* d_partial = nullptr;  // cx [nslots * tile cells]
+  int* d_bin_start = nullptr; // [nbins + 1]
+  SpreadItem* d_items = nullptr;
+  SplitTile* d_split = nullptr;
+  int nitems = 0, nsplit = 0, nslots = 0;
+  int tw_n[8] = {};           // lengths of the twiddle tables below
+  void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n}
+  // GPE workspace
+  void* d_psi1 = nullptr;     // cx [N]
+  void* d_rho = nullptr;      // T [N]
+  void* d_phi = nullptr;      // T [N]
+  void* d_work = nullptr;     // cx [N]
+  void* d_work2 = nullptr;    // cx [N]
+  void* d_kin = nullptr;      // cx [n0 + n1 + n2]: per-axis kinetic phase factors
+  double* d_red = nullptr;    // reduction partials
+  double* h_red = nullptr;    // pinned host copy of reduction results
+  void* d_io_in = nullptr;    // staging for ddi_apply_host
+  void* d_io_out = nullptr;
+  int red_blocks = 0;
+
+  // per-launch CUDA events for ddi_apply_timed (recorded only while `timing` is set)
+  bool timing = false;
+  int nmarks = 0;
+  const char* mark_names[64] = {};
+  cudaEvent_t mark_ev[65] = {};
+  bool ev_created = false;
+  void mark(const char* name, cudaStream_t s) {
+    if (!timing || nmarks >= 64) return;
+    mark_names[nmarks] = name;
+    cudaEventRecord(mark_ev[nmarks + 1], s);
+    ++nmarks;
+  }
+
+  int64_t grid_points() const { return (int64_t)n[0] * n[1] * n[2]; }
+  int64_t fine_points() const { return (int64_t)nf[0] * nf[1] * nf[2]; }
+  size_t real_size() const { return prec == DDI_FP64 ? 8 : 4; }
+  size_t cx_size() const { return prec == DDI_FP64 ? 16 : 8; }
+};
+
+inline const void* twiddles(const Plan& p, int n) {
+  for (int i = 0; i < 8; ++i)
+    if (p.tw_n[i] == n) return p.d_tw[i];
+  return nullptr;
+}
+
+// ---- FFT (fft.cu) ------------------------------------------------------------------
+// In-place batched 1-D FFTs along one axis of a [nz][ny][nx] complex array, unnormalised,
+// dir = -1: e^{-2 pi i jk/n}, dir = +1: e^{+2 pi i jk/n}.  axis 0 = x, 1 = y, 2 = z.
+template <typename T>
+int fft_axis(const Plan& p, cx_t<T>* data, int nx, int ny, int nz, int axis, int dir, cudaStream_t s);
+template <typename T>
+int fft_3d(const Plan& p, cx_t<T>* data, int nx, int ny, int nz, int dir, cudaStream_t s);
+int make_twiddles(Plan& p, int n);
+
+// ---- NUFFT stages (nufft.cu) --------------------------------------------------------
+template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);       // rho -> d_c
+template <typename T> int run_type1(Plan& p, T* phi, cudaStream_t s);             // d_c -> phi
+template <typename T> int run_ddi(Plan& p, const T* rho, T* phi, cudaStream_t s);
+
+}  // namespace ddi
+
+struct ddi_plan_s {
+  ddi::Plan p;
+};

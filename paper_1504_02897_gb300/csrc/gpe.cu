@@ -1,0 +1,631 @@
+// GPE layer on top of the DDI: time-splitting Fourier pseudospectral step (Sec. 4.1,
+// Eq. tssp2, Case I), energies (Sec. 3.2), normalised gradient flow with backward
+// Euler (Sec. 3.1, Eqs. gf-eq2..gffg33) and the adjoint of one TSFP step.
+//
+// Grids are the plan's n[0] x n[1] x n[2] periodic box; Fourier modes are
+// mu_p = 2 pi p / len, p = -n/2..n/2-1 (stored in FFT order).  The FFTs of fft.cu are
+// unnormalised, so every Fourier-space multiplier below carries the 1/N_tot factor.
+// Reductions accumulate in FP64 per thread, per block (fixed order), then one block
+// sums the block partials in a fixed order: results are deterministic.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace ddi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRedMax = 8;  // sums per reduction
+
+struct G3 {
+  int n[3];
+  double len[3];
+};
+
+G3 g3_of(const Plan& p) {
+  G3 g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = p.n[d];
+    g.len[d] = p.desc.len[d] > 0 ? p.desc.len[d] : 1.0;
+  }
+  return g;
+}
+
+__device__ __forceinline__ double mode_mu(int l, int n, double len) {
+  const int pp = l < n / 2 ? l : l - n;
+  return (2.0 * M_PI * (double)pp) / len;
+}
+
+__device__ __forceinline__ void idx3(long long idx, const G3& g, int& x, int& y, int& z) {
+  x = (int)(idx % g.n[0]);
+  const long long r = idx / g.n[0];
+  y = (int)(r % g.n[1]);
+  z = (int)(r / g.n[1]);
+}
+
+__device__ __forceinline__ void sincos_t(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_t(double a, double* s, double* c) { sincos(a, s, c); }
+
+// per-axis factors e^{i f mu_d^2} (FP64 built, rounded once) for separable kinetic phases
+template <typename T>
+__global__ void k_phase_tables(cx_t<T>* tab, G3 g, double f) {
+  const int total = g.n[0] + g.n[1] + g.n[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int d = 0, l = i;
+    while (l >= g.n[d]) {
+      l -= g.n[d];
+      ++d;
+    }
+    const double mu = g.n[d] == 1 ? 0.0 : mode_mu(l, g.n[d], g.len[d]);
+    double s, c;
+    sincos(f * mu * mu, &s, &c);
+    tab[i] = cmk<cx_t<T>>((T)c, (T)s);
+  }
+}
+
+// psihat <- psihat * e^{i f |mu|^2} / N_tot using the per-axis tables
+template <typename T>
+__global__ void k_kinetic(cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ tab, G3 g, T inv_n) {
+  using C = cx_t<T>;
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  const C* tx = tab;
+  const C* ty = tab + g.n[0];
+  const C* tz = ty + g.n[1];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    idx3(i, g, x, y, z);
+    const C f = cmul(cmul(tx[x], ty[y]), tz[z]);
+    a[i] = cscale(cmul(a[i], f), inv_n);
+  }
+}
+
+template <typename T>
+__global__ void k_abs2(const cx_t<T>* __restrict__ psi, T* __restrict__ rho, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cx_t<T> v = psi[i];
+    rho[i] = v.x * v.x + v.y * v.y;
+  }
+}
+
+// psi <- psi exp(-i dt (V + beta rho + lambda Phi)), rho = |psi|^2 (Case I of Eq. tssp2)
+template <typename T>
+__global__ void k_nonlinear(cx_t<T>* __restrict__ psi, const T* __restrict__ V, const T* __restrict__ rho,
+                            const T* __restrict__ phi, T beta, T lam, T dt, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T th = V[i] + beta * rho[i] + lam * phi[i];
+    T s, c;
+    sincos_t(-dt * th, &s, &c);
+    psi[i] = cmul(psi[i], cmk<cx_t<T>>(c, s));
+  }
+}
+
+// ---- FP64 reductions ------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* out) {
+  __shared__ double sh[kRedMax][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += sh[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void block_max(double (&v)[K], double* out) {
+  __shared__ double sh[kRedMax][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if (lane == 0) sh[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = -INFINITY;
+    for (int w = 0; w < kThreads / 32; ++w) s = fmax(s, sh[threadIdx.x][w]);
+    out[threadIdx.x] = s;
+  }
+}
+
+// sums over the grid: mass, V|psi|^2, |psi|^4, Phi|psi|^2 (Phi may be null)
+template <typename T>
+__global__ void k_red_energy(const cx_t<T>* __restrict__ psi, const T* __restrict__ V,
+                             const T* __restrict__ phi, long long total, double* part) {
+  double v[4] = {0, 0, 0, 0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cx_t<T> a = psi[i];
+    const double r = (double)a.x * a.x + (double)a.y * a.y;
+    v[0] += r;
+    v[1] += (double)V[i] * r;
+    v[2] += r * r;
+    if (phi) v[3] += (double)phi[i] * r;
+  }
+  block_sum<4>(v, part + (size_t)blockIdx.x * kRedMax);
+}
+
+// sum |mu|^2 |psihat|^2
+template <typename T>
+__global__ void k_red_kinetic(const cx_t<T>* __restrict__ a, G3 g, double* part) {
+  double v[1] = {0};
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    idx3(i, g, x, y, z);
+    double m2 = 0.0;
+    if (g.n[0] > 1) { const double m = mode_mu(x, g.n[0], g.len[0]); m2 += m * m; }
+    if (g.n[1] > 1) { const double m = mode_mu(y, g.n[1], g.len[1]); m2 += m * m; }
+    if (g.n[2] > 1) { const double m = mode_mu(z, g.n[2], g.len[2]); m2 += m * m; }
+    const cx_t<T> c = a[i];
+    v[0] += m2 * ((double)c.x * c.x + (double)c.y * c.y);
+  }
+  block_sum<1>(v, part + (size_t)blockIdx.x * kRedMax);
+}
+
+// max and -min of W = V + beta |psi|^2 + lambda Phi, and a NaN/Inf flag
+template <typename T>
+__global__ void k_red_wrange(const T* __restrict__ V, const T* __restrict__ rho, const T* __restrict__ phi,
+                             double beta, double lam, long long total, double* part) {
+  double v[3] = {-INFINITY, -INFINITY, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double w = (double)V[i] + beta * (double)rho[i] + (phi ? lam * (double)phi[i] : 0.0);
+    if (!isfinite(w)) v[2] = 1.0;
+    v[0] = fmax(v[0], w);
+    v[1] = fmax(v[1], -w);
+  }
+  block_max<3>(v, part + (size_t)blockIdx.x * kRedMax);
+}
+
+// max |a - b| and max |a|
+template <typename T>
+__global__ void k_red_maxdiff(const cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ b, long long total,
+                              double* part) {
+  double v[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cx_t<T> x = a[i], y = b[i];
+    const double dr = (double)x.x - y.x, di = (double)x.y - y.y;
+    const double d = sqrt(dr * dr + di * di);
+    v[0] = fmax(v[0], isfinite(d) ? d : INFINITY);
+    v[1] = fmax(v[1], sqrt((double)x.x * x.x + (double)x.y * x.y));
+  }
+  block_max<2>(v, part + (size_t)blockIdx.x * kRedMax);
+}
+
+__global__ void k_red_final(const double* part, int blocks, int k, int is_max, double* out) {
+  // one thread per quantity, blocks summed in index order
+  const int t = threadIdx.x;
+  if (t >= k) return;
+  double s = is_max ? -INFINITY : 0.0;
+  for (int b = 0; b < blocks; ++b) {
+    const double x = part[(size_t)b * kRedMax + t];
+    s = is_max ? fmax(s, x) : s + x;
+  }
+  out[t] = s;
+}
+
+// GF: rhs = phi/dt + (alpha - W) cur, W = V + beta rho + lambda Phi
+template <typename T>
+__global__ void k_gf_rhs(const cx_t<T>* __restrict__ phi, const cx_t<T>* __restrict__ cur,
+                         const T* __restrict__ V, const T* __restrict__ rho, const T* __restrict__ dip,
+                         cx_t<T>* __restrict__ out, T beta, T lam, T alpha, T inv_dt, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T w = V[i] + beta * rho[i] + (dip ? lam * dip[i] : (T)0);
+    const T f = alpha - w;
+    const cx_t<T> a = phi[i], c = cur[i];
+    out[i] = cmk<cx_t<T>>(a.x * inv_dt + f * c.x, a.y * inv_dt + f * c.y);
+  }
+}
+
+// GF: divide by (1/dt + alpha + |mu|^2/2) and by N_tot
+template <typename T>
+__global__ void k_gf_solve(cx_t<T>* __restrict__ a, G3 g, double inv_dt_alpha, double inv_n) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    idx3(i, g, x, y, z);
+    double m2 = 0.0;
+    if (g.n[0] > 1) { const double m = mode_mu(x, g.n[0], g.len[0]); m2 += m * m; }
+    if (g.n[1] > 1) { const double m = mode_mu(y, g.n[1], g.len[1]); m2 += m * m; }
+    if (g.n[2] > 1) { const double m = mode_mu(z, g.n[2], g.len[2]); m2 += m * m; }
+    const T f = (T)(inv_n / (inv_dt_alpha + 0.5 * m2));
+    a[i] = cscale(a[i], f);
+  }
+}
+
+template <typename T>
+__global__ void k_scale(cx_t<T>* __restrict__ a, T s, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    a[i] = cscale(a[i], s);
+}
+
+// adjoint, part A: given psi1, rho = |psi1|^2, Phi, g2 (in cot):
+//   e = exp(-i dt theta); r = Re(conj(-i dt psi1 e) g2); grad += dv r;
+//   cot <- conj(e) g2; rout <- r
+template <typename T>
+__global__ void k_adj_a(const cx_t<T>* __restrict__ psi1, const T* __restrict__ V, const T* rho,
+                        const T* __restrict__ phi, cx_t<T>* __restrict__ cot, T* __restrict__ grad,
+                        T* rout, T beta, T lam, T dt, T dv, long long total) {
+  using C = cx_t<T>;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T th = V[i] + beta * rho[i] + lam * phi[i];
+    T s, c;
+    sincos_t(-dt * th, &s, &c);
+    const C e = cmk<C>(c, s);
+    const C psi2 = cmul(psi1[i], e);
+    // -i dt psi2 = dt (psi2.y, -psi2.x); Re(conj(u) g) = u.x g.x + u.y g.y
+    const C g2 = cot[i];
+    const T r = dt * (psi2.y * g2.x - psi2.x * g2.y);
+    grad[i] += dv * r;
+    rout[i] = r;
+    cot[i] = cmul(cconj(e), g2);
+  }
+}
+
+// adjoint, part B: cot += 2 psi1 (beta r + lambda Phi_r)
+template <typename T>
+__global__ void k_adj_b(const cx_t<T>* __restrict__ psi1, const T* __restrict__ r, const T* __restrict__ phir,
+                        cx_t<T>* __restrict__ cot, T beta, T lam, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T sfield = (T)2 * (beta * r[i] + (phir ? lam * phir[i] : (T)0));
+    const cx_t<T> a = psi1[i], c = cot[i];
+    cot[i] = cmk<cx_t<T>>(c.x + sfield * a.x, c.y + sfield * a.y);
+  }
+}
+
+unsigned blocks_for(long long total) {
+  long long b = (total + kThreads - 1) / kThreads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---- host helpers ------------------------------------------------------------------------------
+template <typename T>
+struct Gpe {
+  using C = cx_t<T>;
+  Plan& p;
+  cudaStream_t s;
+  long long N;
+  G3 g;
+
+  Gpe(Plan& pl, cudaStream_t st) : p(pl), s(st), N(pl.grid_points()), g(g3_of(pl)) {}
+
+  int fft(C* a, int dir) { return fft_3d<T>(p, a, p.n[0], p.n[1], p.n[2], dir, s); }
+
+  // a <- F^{-1} e^{i f |mu|^2} F a
+  int kinetic(C* a, double f) {
+    DDI_TRY(fft(a, -1));
+    C* tab = static_cast<C*>(p.d_kin);
+    k_phase_tables<T><<<4, kThreads, 0, s>>>(tab, g, f);
+    DDI_LAUNCH_CHECK();
+    k_kinetic<T><<<blocks_for(N), kThreads, 0, s>>>(a, tab, g, (T)(1.0 / (double)N));
+    DDI_LAUNCH_CHECK();
+    return fft(a, +1);
+  }
+
+  int abs2(const C* a, T* out) {
+    k_abs2<T><<<blocks_for(N), kThreads, 0, s>>>(a, out, N);
+    DDI_LAUNCH_CHECK();
+    return DDI_OK;
+  }
+
+  int reduce(int k, int is_max, double* host_out) {
+    k_red_final<<<1, 32, 0, s>>>(p.d_red, p.red_blocks, k, is_max, p.d_red + (size_t)p.red_blocks * kRedMax);
+    DDI_LAUNCH_CHECK();
+    DDI_CUDA(cudaMemcpyAsync(p.h_red, p.d_red + (size_t)p.red_blocks * kRedMax, sizeof(double) * k,
+                             cudaMemcpyDeviceToHost, s));
+    DDI_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < k; ++i) host_out[i] = p.h_red[i];
+    return DDI_OK;
+  }
+
+  int energy(const C* psi, const T* V, double beta, double lam, gpe_stats* out) {
+    // Phi of |psi|^2 (skipped when lambda = 0)
+    DDI_TRY(abs2(psi, static_cast<T*>(p.d_rho)));
+    const T* phi = nullptr;
+    if (lam != 0.0) {
+      DDI_TRY(run_ddi<T>(p, static_cast<const T*>(p.d_rho), static_cast<T*>(p.d_phi), s));
+      phi = static_cast<const T*>(p.d_phi);
+    }
+    k_red_energy<T><<<p.red_blocks, kThreads, 0, s>>>(psi, V, phi, N, p.d_red);
+    DDI_LAUNCH_CHECK();
+    double sums[4];
+    DDI_TRY(reduce(4, 0, sums));
+    C* w = static_cast<C*>(p.d_work2);
+    DDI_CUDA(cudaMemcpyAsync(w, psi, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+    DDI_TRY(fft(w, -1));
+    k_red_kinetic<T><<<p.red_blocks, kThreads, 0, s>>>(w, g, p.d_red);
+    DDI_LAUNCH_CHECK();
+    double kin;
+    DDI_TRY(reduce(1, 0, &kin));
+    const double dv = p.dv;
+    out->mass = dv * sums[0];
+    out->Ekin = 0.5 * dv / (double)N * kin;
+    out->Epot = dv * sums[1];
+    out->Eint = 0.5 * beta * dv * sums[2];
+    out->Edip = lam != 0.0 ? 0.5 * lam * dv * sums[3] : 0.0;
+    out->E = out->Ekin + out->Epot + out->Eint + out->Edip;
+    out->mu = out->E + out->Eint + out->Edip;
+    out->virial = 2 * out->Ekin - 2 * out->Epot + 3 * out->Eint + 3 * out->Edip;
+    if (!std::isfinite(out->E)) {
+      set_error("energy is not finite");
+      return DDI_ERR_NONFINITE;
+    }
+    return DDI_OK;
+  }
+
+  int normalise(C* a, double* mass_out) {
+    k_red_energy<T><<<p.red_blocks, kThreads, 0, s>>>(a, static_cast<const T*>(p.d_rho), nullptr, N, p.d_red);
+    DDI_LAUNCH_CHECK();
+    double sums[4];
+    DDI_TRY(reduce(1, 0, sums));
+    const double m = p.dv * sums[0];
+    if (!(m > 0.0) || !std::isfinite(m)) {
+      set_error("state has zero or non-finite mass");
+      return DDI_ERR_NONFINITE;
+    }
+    k_scale<T><<<blocks_for(N), kThreads, 0, s>>>(a, (T)(1.0 / std::sqrt(m)), N);
+    DDI_LAUNCH_CHECK();
+    if (mass_out) *mass_out = m;
+    return DDI_OK;
+  }
+
+  int maxdiff(const C* a, const C* b, double* d, double* amax) {
+    k_red_maxdiff<T><<<p.red_blocks, kThreads, 0, s>>>(a, b, N, p.d_red);
+    DDI_LAUNCH_CHECK();
+    double v[2];
+    DDI_TRY(reduce(2, 1, v));
+    *d = v[0];
+    if (amax) *amax = v[1];
+    return DDI_OK;
+  }
+
+  int step(C* psi, const T* V, double beta, double lam, double dt, int nsteps) {
+    T* rho = static_cast<T*>(p.d_rho);
+    T* phi = static_cast<T*>(p.d_phi);
+    // consecutive half kinetic steps merge into one full step between nonlinear steps
+    DDI_TRY(kinetic(psi, -0.25 * dt));
+    for (int k = 0; k < nsteps; ++k) {
+      DDI_TRY(abs2(psi, rho));
+      if (lam != 0.0) {
+        DDI_TRY(run_ddi<T>(p, rho, phi, s));
+      } else {
+        DDI_CUDA(cudaMemsetAsync(phi, 0, sizeof(T) * N, s));
+      }
+      k_nonlinear<T><<<blocks_for(N), kThreads, 0, s>>>(psi, V, rho, phi, (T)beta, (T)lam, (T)dt, N);
+      DDI_LAUNCH_CHECK();
+      DDI_TRY(kinetic(psi, k + 1 < nsteps ? -0.5 * dt : -0.25 * dt));
+    }
+    return DDI_OK;
+  }
+
+  int adjoint(const C* psi_in, C* cot, T* grad, const T* V, double beta, double lam, double dt) {
+    C* psi1 = static_cast<C*>(p.d_psi1);
+    T* rho = static_cast<T*>(p.d_rho);
+    T* phi = static_cast<T*>(p.d_phi);
+    DDI_CUDA(cudaMemcpyAsync(psi1, psi_in, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+    DDI_TRY(kinetic(psi1, -0.25 * dt));
+    DDI_TRY(abs2(psi1, rho));
+    if (lam != 0.0) {
+      DDI_TRY(run_ddi<T>(p, rho, phi, s));
+    } else {
+      DDI_CUDA(cudaMemsetAsync(phi, 0, sizeof(T) * N, s));
+    }
+    DDI_TRY(kinetic(cot, +0.25 * dt));
+    k_adj_a<T><<<blocks_for(N), kThreads, 0, s>>>(psi1, V, rho, phi, cot, grad, rho, (T)beta, (T)lam, (T)dt,
+                                                  (T)p.dv, N);
+    DDI_LAUNCH_CHECK();
+    if (lam != 0.0) DDI_TRY(run_ddi<T>(p, rho, phi, s));
+    k_adj_b<T><<<blocks_for(N), kThreads, 0, s>>>(psi1, rho, lam != 0.0 ? phi : nullptr, cot, (T)beta, (T)lam, N);
+    DDI_LAUNCH_CHECK();
+    return kinetic(cot, +0.25 * dt);
+  }
+
+  int ground_state(C* phi0, const T* V, double beta, double lam, double dt, double tol, int rule,
+                   double inner_tol, int max_steps, int check_every, gpe_stats* out) {
+    C* cur = static_cast<C*>(p.d_psi1);
+    C* nxt = static_cast<C*>(p.d_work);
+    C* prev = static_cast<C*>(p.d_work2);
+    T* rho = static_cast<T*>(p.d_rho);
+    T* dip = static_cast<T*>(p.d_phi);
+    DDI_TRY(normalise(phi0, nullptr));
+    gpe_stats st{};
+    DDI_TRY(energy(phi0, V, beta, lam, &st));
+    double e_prev = st.E;
+    int inner_max_seen = 0;
+    double change = INFINITY;
+    if (check_every < 1) check_every = 1;
+    for (int n = 1; n <= max_steps; ++n) {
+      // W = V + beta |phi|^2 + lambda Phi(|phi|^2) and alpha = (max W + min W) / 2
+      DDI_TRY(abs2(phi0, rho));
+      if (lam != 0.0) DDI_TRY(run_ddi<T>(p, rho, dip, s));
+      k_red_wrange<T><<<p.red_blocks, kThreads, 0, s>>>(V, rho, lam != 0.0 ? dip : nullptr, beta, lam, N, p.d_red);
+      DDI_LAUNCH_CHECK();
+      double wr[3];
+      DDI_TRY(reduce(3, 1, wr));
+      if (wr[2] > 0.0) {
+        set_error("non-finite effective potential at gradient-flow step %d", n);
+        return DDI_ERR_NONFINITE;
+      }
+      const double alpha = 0.5 * (wr[0] - wr[1]);
+      const double inv_dt_alpha = 1.0 / dt + alpha;
+      DDI_CUDA(cudaMemcpyAsync(cur, phi0, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+      int it = 0;
+      for (it = 1; it <= 200; ++it) {
+        k_gf_rhs<T><<<blocks_for(N), kThreads, 0, s>>>(phi0, cur, V, rho, lam != 0.0 ? dip : nullptr, nxt, (T)beta,
+                                                       (T)lam, (T)alpha, (T)(1.0 / dt), N);
+        DDI_LAUNCH_CHECK();
+        DDI_TRY(fft(nxt, -1));
+        k_gf_solve<T><<<blocks_for(N), kThreads, 0, s>>>(nxt, g, inv_dt_alpha, 1.0 / (double)N);
+        DDI_LAUNCH_CHECK();
+        DDI_TRY(fft(nxt, +1));
+        double d;
+        DDI_TRY(maxdiff(nxt, cur, &d, nullptr));
+        C* t = cur;
+        cur = nxt;
+        nxt = t;
+        if (!std::isfinite(d)) {
+          set_error("gradient-flow inner iteration diverged at step %d", n);
+          return DDI_ERR_NONFINITE;
+        }
+        if (d <= inner_tol) break;
+      }
+      if (it > 200) it = 200;
+      inner_max_seen = it > inner_max_seen ? it : inner_max_seen;
+      DDI_TRY(normalise(cur, nullptr));
+      // cur is phi^{n+1}; keep phi^n in prev for the paper's rule
+      DDI_CUDA(cudaMemcpyAsync(prev, phi0, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+      DDI_CUDA(cudaMemcpyAsync(phi0, cur, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+      if (n % check_every == 0 || n == max_steps) {
+        bool done;
+        if (rule == GPE_STOP_PAPER) {
+          double d;
+          DDI_TRY(maxdiff(phi0, prev, &d, nullptr));
+          change = d / dt;
+          done = change <= tol;
+        } else {
+          DDI_TRY(energy(phi0, V, beta, lam, &st));
+          change = std::fabs(st.E - e_prev);
+          e_prev = st.E;
+          done = change < tol;
+        }
+        if (done) {
+          DDI_TRY(energy(phi0, V, beta, lam, &st));
+          st.steps = n;
+          st.inner_max = inner_max_seen;
+          st.last_change = change;
+          *out = st;
+          return DDI_OK;
+        }
+      }
+    }
+    DDI_TRY(energy(phi0, V, beta, lam, &st));
+    st.steps = max_steps;
+    st.inner_max = inner_max_seen;
+    st.last_change = change;
+    *out = st;
+    set_error("gradient flow did not reach tol %.3g in %d steps (last change %.3g)", tol, max_steps, change);
+    return DDI_ERR_NOCONV;
+  }
+};
+
+int check_gpe(ddi_plan plan, const void* a, const void* b) {
+  if (!plan || !a || !b) {
+    set_error("plan and array pointers must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->p.device) {
+    set_error("the current device is not the plan's device");
+    return DDI_ERR_ARG;
+  }
+  return DDI_OK;
+}
+
+bool finite_params(std::initializer_list<double> v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+}  // namespace
+}  // namespace ddi
+
+using ddi::Gpe;
+
+extern "C" {
+
+int gpe_step(ddi_plan plan, void* psi, const void* V, double beta, double lambda, double dt, int nsteps,
+             void* stream) {
+  DDI_TRY(ddi::check_gpe(plan, psi, V));
+  if (nsteps < 0 || !ddi::finite_params({beta, lambda, dt})) {
+    ddi::set_error("nsteps must be >= 0 and beta, lambda, dt finite");
+    return DDI_ERR_ARG;
+  }
+  if (nsteps == 0) return DDI_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->p.prec == DDI_FP64) {
+    Gpe<double> g(plan->p, s);
+    return g.step(static_cast<double2*>(psi), static_cast<const double*>(V), beta, lambda, dt, nsteps);
+  }
+  Gpe<float> g(plan->p, s);
+  return g.step(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, dt, nsteps);
+}
+
+int gpe_energy(ddi_plan plan, const void* psi, const void* V, double beta, double lambda, gpe_stats* out,
+               void* stream) {
+  DDI_TRY(ddi::check_gpe(plan, psi, V));
+  if (!out || !ddi::finite_params({beta, lambda})) {
+    ddi::set_error("out must not be NULL and beta, lambda finite");
+    return DDI_ERR_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->p.prec == DDI_FP64) {
+    Gpe<double> g(plan->p, s);
+    return g.energy(static_cast<const double2*>(psi), static_cast<const double*>(V), beta, lambda, out);
+  }
+  Gpe<float> g(plan->p, s);
+  return g.energy(static_cast<const float2*>(psi), static_cast<const float*>(V), beta, lambda, out);
+}
+
+int gpe_ground_state(ddi_plan plan, void* phi, const void* V, double beta, double lambda, double dt, double tol,
+                     int rule, double inner_tol, int max_steps, int check_every, gpe_stats* out, void* stream) {
+  DDI_TRY(ddi::check_gpe(plan, phi, V));
+  if (!out || !(dt > 0.0) || !(tol > 0.0) || !(inner_tol > 0.0) || max_steps < 1 ||
+      (rule != GPE_STOP_ENERGY && rule != GPE_STOP_PAPER) || !ddi::finite_params({beta, lambda, dt, tol})) {
+    ddi::set_error("invalid gradient-flow arguments (dt, tol, inner_tol > 0; max_steps >= 1; rule 0/1)");
+    return DDI_ERR_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->p.prec == DDI_FP64) {
+    Gpe<double> g(plan->p, s);
+    return g.ground_state(static_cast<double2*>(phi), static_cast<const double*>(V), beta, lambda, dt, tol, rule,
+                          inner_tol, max_steps, check_every, out);
+  }
+  Gpe<float> g(plan->p, s);
+  return g.ground_state(static_cast<float2*>(phi), static_cast<const float*>(V), beta, lambda, dt, tol, rule,
+                        inner_tol, max_steps, check_every, out);
+}
+
+int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V, const void* V, double beta,
+                     double lambda, double dt, void* stream) {
+  DDI_TRY(ddi::check_gpe(plan, psi_in, cot));
+  DDI_TRY(ddi::check_gpe(plan, grad_V, V));
+  if (!ddi::finite_params({beta, lambda, dt})) {
+    ddi::set_error("beta, lambda, dt must be finite");
+    return DDI_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->p.prec == DDI_FP64) {
+    Gpe<double> g(plan->p, s);
+    return g.adjoint(static_cast<const double2*>(psi_in), static_cast<double2*>(cot), static_cast<double*>(grad_V),
+                     static_cast<const double*>(V), beta, lambda, dt);
+  }
+  Gpe<float> g(plan->p, s);
+  return g.adjoint(static_cast<const float2*>(psi_in), static_cast<float2*>(cot), static_cast<float*>(grad_V),
+                   static_cast<const float*>(V), beta, lambda, dt);
+}
+
+}  // extern "C"

@@ -1,0 +1,991 @@
+// NUFFT evaluation of the DDI quadrature sum (Sec. 2.1, Eq. DDI-Trun1).
+//
+//   Phi_j = Re sum_q W_q e^{i k_q.x_j} h^d sum_j' rho_j' e^{-i k_q.x_j'}
+//
+// With t_q = k_q h (per axis) and centred indices j' = j - n/2 the box centre cancels
+// between the two transforms, so the path evaluates
+//   f_q   = sum_j' rho_j' e^{-i t_q.j'}                         (type 2)
+//   c_q   = 2 h^d W_q f_q       over one node of each (k, -k) pair
+//   Phi_j = Re sum_q c_q e^{+i t_q.j'}                            (type 1)
+// (the node set is closed under k -> -k with equal weights and rho is real, so the sum
+// over the pair is twice the real part of one term).  Both transforms use a 2x
+// oversampled grid and the exponential-of-semicircle kernel
+//   psi(x) = exp(beta (sqrt(1 - (2x/w)^2) - 1)), |x| < w/2 (x in fine cells),
+// with deconvolution by its Fourier transform psihat(2 pi j'/nf).
+//
+// Kernels (one launch each):
+//   k_pad        rho / psihat placed at j' mod nf, zero elsewhere      (type-2 prologue)
+//   fft (fft.cu) forward 3 passes
+//   k_interp     f_q = sum over the w^d taps of psi * F, times 2 h^d W_q (one thread per node)
+//   k_spread     owner-computes spread: a CTA owns a fine-grid tile, accumulates every
+//                node whose taps reach it in shared memory (warps own z-planes, so no
+//                atomics), and writes the tile once; tiles with more visits than one
+//                work item takes are split into partial tiles
+//   k_reduce     sums the partial tiles of split tiles
+//   fft          inverse 3 passes
+//   k_crop       Phi_j = Re U_{j' mod nf} / psihat
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "common.cuh"
+
+namespace ddi {
+
+// ---- error reporting -----------------------------------------------------------------
+namespace {
+thread_local std::string g_err;
+}
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+const char* last_error() { return g_err.c_str(); }
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kStage = 64;  // nodes staged per round in k_spread
+
+template <typename T> struct Pos4 { T x, y, z, w; };
+
+__device__ __forceinline__ float es_exp(float v) { return expf(v); }
+__device__ __forceinline__ double es_exp(double v) { return exp(v); }
+__device__ __forceinline__ float es_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double es_sqrt(double v) { return sqrt(v); }
+
+// psi at the W taps of one axis: x_a = a - W/2 - f, f = s - l0 - W/2 in (-1, 0].
+template <typename T, int W>
+__device__ __forceinline__ void es_taps(T f, T beta, T* out) {
+  const T inv_hw = (T)2 / (T)W;
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    const T z = ((T)a - (T)(W / 2) - f) * inv_hw;
+    const T zz = z * z;
+    out[a] = zz < (T)1 ? es_exp(beta * (es_sqrt((T)1 - zz) - (T)1)) : (T)0;
+  }
+}
+
+struct GridDims {
+  int n[3];
+  int nf[3];
+};
+
+// i in [0, 2 nf) -> i mod nf
+__device__ __forceinline__ int wrap1(int i, int nf) { return i >= nf ? i - nf : i; }
+// i in (-nf, 2 nf) -> i mod nf
+__device__ __forceinline__ int wrap2(int i, int nf) { return i < 0 ? i + nf : (i >= nf ? i - nf : i); }
+
+// ---- type-2 prologue -------------------------------------------------------------------
+template <typename T>
+__global__ void k_pad(const T* __restrict__ rho, cx_t<T>* __restrict__ fine,
+                      const T* __restrict__ dc, GridDims g) {
+  using C = cx_t<T>;
+  const long long total = (long long)g.nf[0] * g.nf[1] * g.nf[2];
+  const T* dcx = dc;
+  const T* dcy = dc + g.n[0];
+  const T* dcz = dcy + g.n[1];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int lx = (int)(idx % g.nf[0]);
+    const long long r = idx / g.nf[0];
+    const int ly = (int)(r % g.nf[1]);
+    const int lz = (int)(r / g.nf[1]);
+    int j[3];
+    const int l[3] = {lx, ly, lz};
+    bool inside = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int hn = g.n[d] / 2;
+      if (g.n[d] == 1) {
+        j[d] = 0;
+      } else if (l[d] < hn) {
+        j[d] = l[d] + hn;
+      } else if (l[d] >= g.nf[d] - hn) {
+        j[d] = l[d] - g.nf[d] + hn;
+      } else {
+        inside = false;
+        j[d] = 0;
+      }
+    }
+    T v = (T)0;
+    if (inside) {
+      v = rho[((long long)j[2] * g.n[1] + j[1]) * g.n[0] + j[0]] * (dcx[j[0]] * dcy[j[1]] * dcz[j[2]]);
+    }
+    fine[idx] = cmk<C>(v, (T)0);
+  }
+}
+
+// ---- type-1 epilogue ---------------------------------------------------------------------
+template <typename T>
+__global__ void k_crop(const cx_t<T>* __restrict__ fine, T* __restrict__ phi,
+                       const T* __restrict__ dc, GridDims g) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  const T* dcx = dc;
+  const T* dcy = dc + g.n[0];
+  const T* dcz = dcy + g.n[1];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int jx = (int)(idx % g.n[0]);
+    const long long r = idx / g.n[0];
+    const int jy = (int)(r % g.n[1]);
+    const int jz = (int)(r / g.n[1]);
+    const int lx = (jx - g.n[0] / 2 + g.nf[0]) % g.nf[0];
+    const int ly = (jy - g.n[1] / 2 + g.nf[1]) % g.nf[1];
+    const int lz = (jz - g.n[2] / 2 + g.nf[2]) % g.nf[2];
+    const T u = fine[((long long)lz * g.nf[1] + ly) * g.nf[0] + lx].x;
+    phi[idx] = u * (dcx[jx] * dcy[jy] * dcz[jz]);
+  }
+}
+
+// ---- interpolation (type 2) -----------------------------------------------------------------
+template <typename T, int W, int DIM>
+__global__ void __launch_bounds__(kThreads)
+    k_interp(const cx_t<T>* __restrict__ fine, const ushort4* __restrict__ l0,
+             const Pos4<T>* __restrict__ pos, cx_t<T>* __restrict__ out, long long count,
+             GridDims g, T beta) {
+  using C = cx_t<T>;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const ushort4 s = l0[i];
+  const Pos4<T> p = pos[i];
+  T kx[W], ky[W];
+  es_taps<T, W>(p.x, beta, kx);
+  es_taps<T, W>(p.y, beta, ky);
+  T ar = 0, ai = 0;
+  if (DIM == 3) {
+    const T inv_hw = (T)2 / (T)W;
+#pragma unroll 1
+    for (int az = 0; az < W; ++az) {
+      // z weight computed on the fly so that no register array is indexed by az
+      const T z = ((T)az - (T)(W / 2) - p.z) * inv_hw;
+      const T wz = z * z < (T)1 ? es_exp(beta * (es_sqrt((T)1 - z * z) - (T)1)) : (T)0;
+      const long long zoff = (long long)wrap1(s.z + az, g.nf[2]) * g.nf[1];
+      T zr = 0, zi = 0;
+#pragma unroll
+      for (int ay = 0; ay < W; ++ay) {
+        const C* row = fine + (zoff + wrap1(s.y + ay, g.nf[1])) * g.nf[0];
+        T rr = 0, ri = 0;
+#pragma unroll
+        for (int ax = 0; ax < W; ++ax) {
+          const C v = __ldg(row + wrap1(s.x + ax, g.nf[0]));
+          rr += kx[ax] * v.x;
+          ri += kx[ax] * v.y;
+        }
+        zr += ky[ay] * rr;
+        zi += ky[ay] * ri;
+      }
+      ar += wz * zr;
+      ai += wz * zi;
+    }
+  } else {
+#pragma unroll
+    for (int ay = 0; ay < W; ++ay) {
+      const C* row = fine + (long long)wrap1(s.y + ay, g.nf[1]) * g.nf[0];
+      T rr = 0, ri = 0;
+#pragma unroll
+      for (int ax = 0; ax < W; ++ax) {
+        const C v = __ldg(row + wrap1(s.x + ax, g.nf[0]));
+        rr += kx[ax] * v.x;
+        ri += kx[ax] * v.y;
+      }
+      ar += ky[ay] * rr;
+      ai += ky[ay] * ri;
+    }
+  }
+  out[i] = cmk<C>(p.w * ar, p.w * ai);
+}
+
+// ---- spreading (type 1) ------------------------------------------------------------------------
+struct SpreadArgs {
+  GridDims g;
+  int tile[3];
+  int ntile[3];
+  const SpreadItem* items;
+  const int* bin_start;
+  const ushort4* l0;
+  const void* pos;
+  const void* c;
+  void* fine;
+  void* partial;
+};
+
+template <typename T, int W, int DIM>
+__global__ void __launch_bounds__(kThreads) k_spread(SpreadArgs a, T beta) {
+  using C = cx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
+  const int cells = TX * TY * TZ;
+  C* acc = reinterpret_cast<C*>(smem_raw);
+  C* cv = acc + cells;                                   // [kStage]
+  T* kv = reinterpret_cast<T*>(cv + kStage);             // [kStage][3][W]
+  int* lv = reinterpret_cast<int*>(kv + kStage * 3 * W); // [kStage][3]
+  __shared__ int nb_begin[8], nb_count[8], nb_prefix[9];
+
+  const SpreadItem it = a.items[blockIdx.x];
+  const int tx = it.tile % a.ntile[0];
+  const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
+  const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
+  const int T0x = tx * TX, T0y = ty * TY, T0z = tz * TZ;
+  if (threadIdx.x == 0) {
+    // visit list: own bin and the lower neighbours (offset 1 exists only with >= 2 tiles)
+    int k = 0;
+    nb_prefix[0] = 0;
+    for (int dz = 0; dz < (DIM == 3 && a.ntile[2] > 1 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < (a.ntile[1] > 1 ? 2 : 1); ++dy)
+        for (int dx = 0; dx < (a.ntile[0] > 1 ? 2 : 1); ++dx) {
+          const int bx = (tx - dx + a.ntile[0]) % a.ntile[0];
+          const int by = (ty - dy + a.ntile[1]) % a.ntile[1];
+          const int bz = (tz - dz + a.ntile[2]) % a.ntile[2];
+          const int b = (bz * a.ntile[1] + by) * a.ntile[0] + bx;
+          nb_begin[k] = a.bin_start[b];
+          nb_count[k] = a.bin_start[b + 1] - a.bin_start[b];
+          nb_prefix[k + 1] = nb_prefix[k] + nb_count[k];
+          ++k;
+        }
+    for (; k < 8; ++k) {
+      nb_begin[k] = 0;
+      nb_count[k] = 0;
+      nb_prefix[k + 1] = nb_prefix[k];
+    }
+  }
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) acc[i] = cmk<C>((T)0, (T)0);
+  __syncthreads();
+
+  const Pos4<T>* pos = static_cast<const Pos4<T>*>(a.pos);
+  const C* cin = static_cast<const C*>(a.c);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int v0 = it.vbeg; v0 < it.vend; v0 += kStage) {
+    const int cnt = min(kStage, it.vend - v0);
+    if (threadIdx.x < cnt) {
+      const int v = v0 + threadIdx.x;
+      int k = 0;
+      while (v >= nb_prefix[k + 1]) ++k;
+      const int node = nb_begin[k] + (v - nb_prefix[k]);
+      const ushort4 s = a.l0[node];
+      const Pos4<T> p = pos[node];
+      T* kk = kv + threadIdx.x * 3 * W;
+      es_taps<T, W>(p.x, beta, kk);
+      es_taps<T, W>(p.y, beta, kk + W);
+      if (DIM == 3) es_taps<T, W>(p.z, beta, kk + 2 * W);
+      cv[threadIdx.x] = cin[node];
+      lv[threadIdx.x * 3 + 0] = s.x;
+      lv[threadIdx.x * 3 + 1] = s.y;
+      lv[threadIdx.x * 3 + 2] = s.z;
+    }
+    __syncthreads();
+    for (int k = 0; k < cnt; ++k) {
+      const T* kk = kv + k * 3 * W;
+      const C cq = cv[k];
+      const int sx = lv[k * 3], sy = lv[k * 3 + 1], sz = lv[k * 3 + 2];
+      if (DIM == 3) {
+        // warp `warp` owns the local z-planes lz with lz % kWarps == warp
+        for (int az = 0; az < W; ++az) {
+          const int lz = wrap2(sz + az - T0z, a.g.nf[2]);
+          if (lz >= TZ || (lz % kWarps) != warp) continue;
+          const T wz = kk[2 * W + az];
+          const T czr = cq.x * wz, czi = cq.y * wz;
+          C* plane = acc + lz * TY * TX;
+          for (int pidx = lane; pidx < W * W; pidx += 32) {
+            const int ay = pidx / W, ax = pidx - ay * W;
+            const int ly = wrap2(sy + ay - T0y, a.g.nf[1]);
+            const int lx = wrap2(sx + ax - T0x, a.g.nf[0]);
+            if (ly < TY && lx < TX) {
+              const T wyx = kk[W + ay] * kk[ax];
+              C* cell = plane + ly * TX + lx;
+              C cur = *cell;
+              cur.x += czr * wyx;
+              cur.y += czi * wyx;
+              *cell = cur;
+            }
+          }
+        }
+      } else {
+        // 2D: warp owns local rows ly with ly % kWarps == warp, lanes take the x taps
+        for (int ay = 0; ay < W; ++ay) {
+          const int ly = wrap2(sy + ay - T0y, a.g.nf[1]);
+          if (ly >= TY || (ly % kWarps) != warp) continue;
+          const T wy = kk[W + ay];
+          for (int ax = lane; ax < W; ax += 32) {
+            const int lx = wrap2(sx + ax - T0x, a.g.nf[0]);
+            if (lx < TX) {
+              const T wyx = wy * kk[ax];
+              C* cell = acc + ly * TX + lx;
+              C cur = *cell;
+              cur.x += cq.x * wyx;
+              cur.y += cq.y * wyx;
+              *cell = cur;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // write the tile (or this item's partial tile)
+  if (it.slot < 0) {
+    C* fine = static_cast<C*>(a.fine);
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+      const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+      const long long off = ((long long)(T0z + lz) * a.g.nf[1] + (T0y + ly)) * a.g.nf[0] + (T0x + lx);
+      fine[off] = acc[i];
+    }
+  } else {
+    C* part = static_cast<C*>(a.partial) + (long long)it.slot * cells;
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) part[i] = acc[i];
+  }
+}
+
+template <typename T>
+__global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __restrict__ partial,
+                         cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx,
+                         int nty) {
+  using C = cx_t<T>;
+  const SplitTile st = split[blockIdx.x];
+  const int cells = TX * TY * TZ;
+  const int tx = st.tile % ntx, ty = (st.tile / ntx) % nty, tz = st.tile / (ntx * nty);
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    T sr = 0, si = 0;
+    for (int k = 0; k < st.nslots; ++k) {
+      const C v = partial[(long long)(st.slot0 + k) * cells + i];
+      sr += v.x;
+      si += v.y;
+    }
+    const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+    const long long off =
+        ((long long)(tz * TZ + lz) * g.nf[1] + (ty * TY + ly)) * g.nf[0] + (tx * TX + lx);
+    fine[off] = cmk<C>(sr, si);
+  }
+}
+
+// ---- launch helpers ----------------------------------------------------------------------------
+GridDims dims_of(const Plan& p) {
+  GridDims g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = p.n[d];
+    g.nf[d] = p.nf[d];
+  }
+  return g;
+}
+
+unsigned grid_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+template <typename T, int W, int DIM>
+int launch_interp(const Plan& p, cudaStream_t s) {
+  const long long cnt = p.Mh;
+  k_interp<T, W, DIM><<<(unsigned)((cnt + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      static_cast<const cx_t<T>*>(p.d_fine), static_cast<const ushort4*>(p.d_l0),
+      static_cast<const Pos4<T>*>(p.d_pos), static_cast<cx_t<T>*>(p.d_c), cnt, dims_of(p), (T)p.beta);
+  DDI_LAUNCH_CHECK();
+  return DDI_OK;
+}
+
+size_t spread_smem(const Plan& p) {
+  const size_t cells = (size_t)p.tile[0] * p.tile[1] * p.tile[2];
+  const size_t rs = p.real_size();
+  return cells * p.cx_size() + kStage * p.cx_size() + (size_t)kStage * 3 * p.w * rs + kStage * 3 * sizeof(int);
+}
+
+template <typename T, int W, int DIM>
+int launch_spread(const Plan& p, cudaStream_t s) {
+  SpreadArgs a;
+  a.g = dims_of(p);
+  for (int d = 0; d < 3; ++d) {
+    a.tile[d] = p.tile[d];
+    a.ntile[d] = p.ntile[d];
+  }
+  a.items = p.d_items;
+  a.bin_start = p.d_bin_start;
+  a.l0 = static_cast<const ushort4*>(p.d_l0);
+  a.pos = p.d_pos;
+  a.c = p.d_c;
+  a.fine = p.d_fine;
+  a.partial = p.d_partial;
+  const size_t smem = spread_smem(p);
+  auto kern = k_spread<T, W, DIM>;
+  if (smem > 48 * 1024) {
+    DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  kern<<<p.nitems, kThreads, smem, s>>>(a, (T)p.beta);
+  DDI_LAUNCH_CHECK();
+  const_cast<Plan&>(p).mark("spread", s);
+  if (p.nsplit > 0) {
+    k_reduce<T><<<p.nsplit, kThreads, 0, s>>>(p.d_split, static_cast<const cx_t<T>*>(p.d_partial),
+                                              static_cast<cx_t<T>*>(p.d_fine), dims_of(p), p.tile[0],
+                                              p.tile[1], p.tile[2], p.ntile[0], p.ntile[1]);
+    DDI_LAUNCH_CHECK();
+    const_cast<Plan&>(p).mark("spread_reduce", s);
+  }
+  return DDI_OK;
+}
+
+template <typename T, int DIM>
+int interp_w(const Plan& p, cudaStream_t s) {
+  if (sizeof(T) == 4) {
+    switch (p.w) {
+      case 6: return launch_interp<T, 6, DIM>(p, s);
+      case 8: return launch_interp<T, 8, DIM>(p, s);
+    }
+  } else {
+    switch (p.w) {
+      case 10: return launch_interp<T, 10, DIM>(p, s);
+      case 12: return launch_interp<T, 12, DIM>(p, s);
+      case 14: return launch_interp<T, 14, DIM>(p, s);
+      case 16: return launch_interp<T, 16, DIM>(p, s);
+    }
+  }
+  set_error("kernel width %d not built for this precision", p.w);
+  return DDI_ERR_ARG;
+}
+
+template <typename T, int DIM>
+int spread_w(const Plan& p, cudaStream_t s) {
+  if (sizeof(T) == 4) {
+    switch (p.w) {
+      case 6: return launch_spread<T, 6, DIM>(p, s);
+      case 8: return launch_spread<T, 8, DIM>(p, s);
+    }
+  } else {
+    switch (p.w) {
+      case 10: return launch_spread<T, 10, DIM>(p, s);
+      case 12: return launch_spread<T, 12, DIM>(p, s);
+      case 14: return launch_spread<T, 14, DIM>(p, s);
+      case 16: return launch_spread<T, 16, DIM>(p, s);
+    }
+  }
+  set_error("kernel width %d not built for this precision", p.w);
+  return DDI_ERR_ARG;
+}
+
+}  // namespace
+
+template <typename T>
+int run_type2(Plan& p, const T* rho, cudaStream_t s) {
+  using C = cx_t<T>;
+  C* fine = static_cast<C*>(p.d_fine);
+  k_pad<T><<<grid_for(p.fine_points(), kThreads), kThreads, 0, s>>>(rho, fine, static_cast<const T*>(p.d_deconv),
+                                                                     dims_of(p));
+  DDI_LAUNCH_CHECK();
+  p.mark("pad", s);
+  static const char* names[3] = {"fft_x_fwd", "fft_y_fwd", "fft_z_fwd"};
+  for (int a = 0; a < p.dim; ++a) {
+    DDI_TRY(fft_axis<T>(p, fine, p.nf[0], p.nf[1], p.nf[2], a, -1, s));
+    p.mark(names[a], s);
+  }
+  DDI_TRY((p.dim == 3 ? interp_w<T, 3>(p, s) : interp_w<T, 2>(p, s)));
+  p.mark("interp", s);
+  return DDI_OK;
+}
+
+template <typename T>
+int run_type1(Plan& p, T* phi, cudaStream_t s) {
+  using C = cx_t<T>;
+  C* fine = static_cast<C*>(p.d_fine);
+  DDI_TRY(p.dim == 3 ? (spread_w<T, 3>(p, s)) : (spread_w<T, 2>(p, s)));
+  static const char* names[3] = {"fft_x_inv", "fft_y_inv", "fft_z_inv"};
+  for (int a = 0; a < p.dim; ++a) {
+    DDI_TRY(fft_axis<T>(p, fine, p.nf[0], p.nf[1], p.nf[2], a, +1, s));
+    p.mark(names[a], s);
+  }
+  k_crop<T><<<grid_for(p.grid_points(), kThreads), kThreads, 0, s>>>(fine, phi, static_cast<const T*>(p.d_deconv),
+                                                                     dims_of(p));
+  DDI_LAUNCH_CHECK();
+  p.mark("crop", s);
+  return DDI_OK;
+}
+
+template <typename T>
+int run_ddi(Plan& p, const T* rho, T* phi, cudaStream_t s) {
+  DDI_TRY(run_type2<T>(p, rho, s));
+  return run_type1<T>(p, phi, s);
+}
+
+template int run_type2<float>(Plan&, const float*, cudaStream_t);
+template int run_type2<double>(Plan&, const double*, cudaStream_t);
+template int run_type1<float>(Plan&, float*, cudaStream_t);
+template int run_type1<double>(Plan&, double*, cudaStream_t);
+template int run_ddi<float>(Plan&, const float*, float*, cudaStream_t);
+template int run_ddi<double>(Plan&, const double*, double*, cudaStream_t);
+
+// ---- plan construction ----------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+void fill_pos(const std::vector<double>& f, const std::vector<double>& sc, std::vector<unsigned char>& out) {
+  const size_t n = sc.size();
+  out.resize(n * sizeof(Pos4<T>));
+  Pos4<T>* o = reinterpret_cast<Pos4<T>*>(out.data());
+  for (size_t i = 0; i < n; ++i) {
+    o[i].x = (T)f[3 * i];
+    o[i].y = (T)f[3 * i + 1];
+    o[i].z = (T)f[3 * i + 2];
+    o[i].w = (T)sc[i];
+  }
+}
+
+int dev_alloc(Plan& p, void** ptr, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes for %s failed", bytes, what);
+    return DDI_ERR_OOM;
+  }
+  p.bytes += bytes;
+  return DDI_OK;
+}
+
+void free_plan(Plan& p) {
+  void* ptrs[] = {p.d_l0, p.d_pos, p.d_c, p.d_deconv, p.d_fine, p.d_partial, p.d_bin_start, p.d_items,
+                  p.d_split, p.d_psi1, p.d_rho, p.d_phi, p.d_work, p.d_work2, p.d_kin, p.d_red, p.d_io_in, p.d_io_out};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (void*& t : p.d_tw)
+    if (t) {
+      cudaFree(t);
+      t = nullptr;
+    }
+  if (p.h_red) cudaFreeHost(p.h_red);
+  if (p.ev_created)
+    for (cudaEvent_t& e : p.mark_ev) cudaEventDestroy(e);
+}
+
+void choose_tile(Plan& p) {
+  // Tiles must be at least w - 1 cells per axis (so a node's taps reach only its own
+  // tile and the next one) and divide the fine grid.
+  auto pick = [&](int want, int need, int nf) {
+    // largest divisor of nf in [need, want], else the smallest divisor >= need
+    for (int t = std::min(want, nf); t >= need && t >= 1; --t)
+      if (nf % t == 0) return t;
+    for (int t = need; t <= nf; ++t)
+      if (nf % t == 0) return t;
+    return nf;
+  };
+  const int need = p.w - 1;
+  int want[3];
+  if (p.dim == 3) {
+    if (p.prec == DDI_FP32) {
+      want[0] = 16; want[1] = 16; want[2] = 8;
+    } else {
+      want[0] = 16; want[1] = 16; want[2] = 16;
+    }
+  } else {
+    want[0] = 32; want[1] = 32; want[2] = 1;
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (p.desc.tile[d] > 0) want[d] = p.desc.tile[d];
+    if (d < p.dim && want[d] < need) want[d] = need;
+    p.tile[d] = d < p.dim ? pick(want[d], need, p.nf[d]) : 1;
+    p.ntile[d] = p.nf[d] / p.tile[d];
+  }
+}
+
+}  // namespace
+
+int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
+  std::string err;
+  DDI_TRY([&]() {
+    int s = normalise_desc(desc_in, &p.desc, &err);
+    if (s != DDI_OK) set_error("%s", err.c_str());
+    return s;
+  }());
+  const ddi_plan_desc& d = p.desc;
+  DDI_CUDA(cudaGetDevice(&p.device));
+  p.dim = d.dim;
+  p.prec = d.precision;
+  p.dv = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    p.n[a] = a < d.dim ? d.n[a] : 1;
+    p.nf[a] = a < d.dim ? 2 * d.n[a] : 1;
+    p.h[a] = a < d.dim ? d.len[a] / (double)d.n[a] : 1.0;
+    if (a < d.dim) p.dv *= p.h[a];
+  }
+  p.w = kernel_width(d);
+  p.beta = kernel_beta(p.w);
+  build_quadrature(d, &p.quad);
+  p.M = p.quad.M;
+  choose_tile(p);
+
+  // one node of each (k, -k) pair: the first half of the azimuth
+  const int nphi = d.nphi, half = nphi / 2;
+  std::vector<int64_t> qs;
+  qs.reserve(p.M / 2);
+  for (int64_t q = 0; q < p.M; ++q)
+    if ((q % nphi) < half) qs.push_back(q);
+  p.Mh = (int64_t)qs.size();
+  const int dim = d.dim;
+  std::vector<int> bin(p.Mh);
+  std::vector<unsigned short> l0w(3 * p.Mh, 0);
+  std::vector<double> fr(3 * p.Mh, 0.0), sc(p.Mh);
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int64_t q = qs[i];
+    int bc[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      const double k = p.quad.k[dim * q + a];
+      const int64_t l0 = fine_start(k, p.h[a], p.nf[a], p.w);
+      const double scale = (p.h[a] * (double)p.nf[a]) / (2.0 * M_PI);
+      const double s = k * scale;
+      fr[3 * i + a] = (s - (double)l0) - 0.5 * (double)p.w;
+      const int64_t wr = ((l0 % p.nf[a]) + p.nf[a]) % p.nf[a];
+      l0w[3 * i + a] = (unsigned short)wr;
+      bc[a] = (int)(wr / p.tile[a]);
+    }
+    bin[i] = (bc[2] * p.ntile[1] + bc[1]) * p.ntile[0] + bc[0];
+    sc[i] = 2.0 * p.dv * p.quad.W[q];
+  }
+  p.nbins = p.ntile[0] * p.ntile[1] * p.ntile[2];
+  std::vector<int64_t> perm(p.Mh);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return bin[a] < bin[b]; });
+  std::vector<int> bin_start(p.nbins + 1, 0);
+  for (int64_t i = 0; i < p.Mh; ++i) bin_start[bin[i] + 1]++;
+  for (int b = 0; b < p.nbins; ++b) bin_start[b + 1] += bin_start[b];
+  p.order.resize(p.Mh);
+  std::vector<ushort4> l0s(p.Mh);
+  std::vector<double> frs(3 * p.Mh), scs(p.Mh);
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int64_t o = perm[i];
+    p.order[i] = qs[o];
+    l0s[i] = make_ushort4(l0w[3 * o], l0w[3 * o + 1], l0w[3 * o + 2], 0);
+    for (int a = 0; a < 3; ++a) frs[3 * i + a] = fr[3 * o + a];
+    scs[i] = sc[o];
+  }
+
+  // spread work list: per tile, its visit count (own bin + lower neighbours), split in chunks
+  std::vector<int> visits(p.nbins, 0);
+  long long total = 0;
+  for (int tz = 0; tz < p.ntile[2]; ++tz)
+    for (int ty = 0; ty < p.ntile[1]; ++ty)
+      for (int tx = 0; tx < p.ntile[0]; ++tx) {
+        int v = 0;
+        for (int dz = 0; dz < (dim == 3 && p.ntile[2] > 1 ? 2 : 1); ++dz)
+          for (int dy = 0; dy < (p.ntile[1] > 1 ? 2 : 1); ++dy)
+            for (int dx = 0; dx < (p.ntile[0] > 1 ? 2 : 1); ++dx) {
+              const int bx = (tx - dx + p.ntile[0]) % p.ntile[0];
+              const int by = (ty - dy + p.ntile[1]) % p.ntile[1];
+              const int bz = (tz - dz + p.ntile[2]) % p.ntile[2];
+              const int b = (bz * p.ntile[1] + by) * p.ntile[0] + bx;
+              v += bin_start[b + 1] - bin_start[b];
+            }
+        visits[(tz * p.ntile[1] + ty) * p.ntile[0] + tx] = v;
+        total += v;
+      }
+  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(1024, total / (152LL * 8));
+  std::vector<SpreadItem> items;
+  std::vector<SplitTile> split;
+  int slot = 0;
+  for (int t = 0; t < p.nbins; ++t) {
+    const int v = visits[t];
+    if (v <= p.chunk) {
+      items.push_back(SpreadItem{t, 0, v, -1});
+    } else {
+      const int nch = (v + p.chunk - 1) / p.chunk;
+      split.push_back(SplitTile{t, slot, nch, 0});
+      for (int c = 0; c < nch; ++c)
+        items.push_back(SpreadItem{t, c * p.chunk, std::min(v, (c + 1) * p.chunk), slot + c});
+      slot += nch;
+    }
+  }
+  // heaviest items first so the long ones start early
+  std::stable_sort(items.begin(), items.end(),
+                   [](const SpreadItem& a, const SpreadItem& b) { return (a.vend - a.vbeg) > (b.vend - b.vbeg); });
+  p.nitems = (int)items.size();
+  p.nsplit = (int)split.size();
+  p.nslots = slot;
+
+  // deconvolution factors 1/psihat(2 pi j'/nf), j' = j - n/2
+  std::vector<double> dc;
+  for (int a = 0; a < 3; ++a) {
+    for (int j = 0; j < p.n[a]; ++j) {
+      if (p.n[a] == 1) {
+        dc.push_back(1.0);
+      } else {
+        const double xi = 2.0 * M_PI * (double)(j - p.n[a] / 2) / (double)p.nf[a];
+        dc.push_back(1.0 / es_kernel_hat(xi, p.w, p.beta));
+      }
+    }
+  }
+
+  // device allocations
+  const size_t rs = p.real_size(), cs = p.cx_size();
+  const size_t cells = (size_t)p.tile[0] * p.tile[1] * p.tile[2];
+  DDI_TRY(dev_alloc(p, &p.d_l0, sizeof(ushort4) * p.Mh, "node taps"));
+  DDI_TRY(dev_alloc(p, &p.d_pos, 4 * rs * p.Mh, "node positions"));
+  DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
+  DDI_TRY(dev_alloc(p, &p.d_deconv, rs * dc.size(), "deconvolution"));
+  DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
+  DDI_TRY(dev_alloc(p, &p.d_partial, cs * cells * std::max(1, p.nslots), "partial tiles"));
+  DDI_TRY(dev_alloc(p, (void**)&p.d_bin_start, sizeof(int) * bin_start.size(), "bins"));
+  DDI_TRY(dev_alloc(p, (void**)&p.d_items, sizeof(SpreadItem) * items.size(), "work items"));
+  DDI_TRY(dev_alloc(p, (void**)&p.d_split, sizeof(SplitTile) * std::max<size_t>(1, split.size()), "split tiles"));
+  const size_t N = (size_t)p.grid_points();
+  DDI_TRY(dev_alloc(p, &p.d_psi1, cs * N, "gpe psi1"));
+  DDI_TRY(dev_alloc(p, &p.d_rho, rs * N, "gpe rho"));
+  DDI_TRY(dev_alloc(p, &p.d_phi, rs * N, "gpe phi"));
+  DDI_TRY(dev_alloc(p, &p.d_work, cs * N, "gpe work"));
+  DDI_TRY(dev_alloc(p, &p.d_work2, cs * N, "gpe work2"));
+  DDI_TRY(dev_alloc(p, &p.d_kin, cs * (p.n[0] + p.n[1] + p.n[2]), "kinetic tables"));
+  p.red_blocks = 1024;
+  DDI_TRY(dev_alloc(p, (void**)&p.d_red, sizeof(double) * 16 * (p.red_blocks + 1), "reductions"));
+  if (cudaMallocHost((void**)&p.h_red, sizeof(double) * 64) != cudaSuccess) {
+    set_error("cudaMallocHost failed");
+    return DDI_ERR_OOM;
+  }
+  DDI_TRY(dev_alloc(p, &p.d_io_in, rs * N, "host io in"));
+  DDI_TRY(dev_alloc(p, &p.d_io_out, rs * N, "host io out"));
+
+  std::vector<unsigned char> posb, dcb(rs * dc.size());
+  if (p.prec == DDI_FP64) {
+    fill_pos<double>(frs, scs, posb);
+    memcpy(dcb.data(), dc.data(), rs * dc.size());
+  } else {
+    fill_pos<float>(frs, scs, posb);
+    for (size_t i = 0; i < dc.size(); ++i) {
+      float v = (float)dc[i];
+      memcpy(dcb.data() + 4 * i, &v, 4);
+    }
+  }
+  DDI_CUDA(cudaMemcpyAsync(p.d_l0, l0s.data(), sizeof(ushort4) * p.Mh, cudaMemcpyHostToDevice, stream));
+  DDI_CUDA(cudaMemcpyAsync(p.d_pos, posb.data(), posb.size(), cudaMemcpyHostToDevice, stream));
+  DDI_CUDA(cudaMemcpyAsync(p.d_deconv, dcb.data(), dcb.size(), cudaMemcpyHostToDevice, stream));
+  DDI_CUDA(cudaMemcpyAsync(p.d_bin_start, bin_start.data(), sizeof(int) * bin_start.size(), cudaMemcpyHostToDevice,
+                           stream));
+  DDI_CUDA(cudaMemcpyAsync(p.d_items, items.data(), sizeof(SpreadItem) * items.size(), cudaMemcpyHostToDevice,
+                           stream));
+  if (!split.empty())
+    DDI_CUDA(cudaMemcpyAsync(p.d_split, split.data(), sizeof(SplitTile) * split.size(), cudaMemcpyHostToDevice,
+                             stream));
+  for (int a = 0; a < 3; ++a) {
+    if (p.nf[a] > 1) DDI_TRY(make_twiddles(p, p.nf[a]));
+    if (p.n[a] > 1) DDI_TRY(make_twiddles(p, p.n[a]));
+  }
+  // the host vectors above die with this frame: finish the uploads first
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  if (spread_smem(p) > 200 * 1024) {
+    set_error("spread tile needs %zu bytes of shared memory; choose a smaller tile", spread_smem(p));
+    return DDI_ERR_ARG;
+  }
+  return DDI_OK;
+}
+
+void destroy_plan(Plan& p) { free_plan(p); }
+
+}  // namespace ddi
+
+// ==== C ABI ======================================================================================
+using ddi::Plan;
+
+extern "C" {
+
+const char* ddi_status_str(int status) {
+  switch (status) {
+    case DDI_OK: return "DDI_OK";
+    case DDI_ERR_ARG: return "DDI_ERR_ARG: invalid argument";
+    case DDI_ERR_CUDA: return "DDI_ERR_CUDA: CUDA runtime error";
+    case DDI_ERR_OOM: return "DDI_ERR_OOM: device allocation failed";
+    case DDI_ERR_NONFINITE: return "DDI_ERR_NONFINITE: NaN or Inf encountered";
+    case DDI_ERR_TIMEOUT: return "DDI_ERR_TIMEOUT: bounded device wait gave up";
+    case DDI_ERR_NOCONV: return "DDI_ERR_NOCONV: iteration limit reached";
+    default: return "unknown ddi status";
+  }
+}
+
+const char* ddi_last_error(void) { return ddi::last_error(); }
+
+int ddi_quadrature_tables(const ddi_plan_desc* desc, int64_t* M, double* k, double* W, int32_t* l0) {
+  ddi_plan_desc d;
+  std::string err;
+  int s = ddi::normalise_desc(desc, &d, &err);
+  if (s != DDI_OK) {
+    ddi::set_error("%s", err.c_str());
+    return s;
+  }
+  if (!M) {
+    ddi::set_error("M must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  ddi::QuadTables t;
+  ddi::build_quadrature(d, &t);
+  *M = t.M;
+  if (k) memcpy(k, t.k.data(), sizeof(double) * t.k.size());
+  if (W) memcpy(W, t.W.data(), sizeof(double) * t.W.size());
+  if (l0) {
+    const int w = ddi::kernel_width(d);
+    for (int64_t q = 0; q < t.M; ++q)
+      for (int a = 0; a < d.dim; ++a)
+        l0[d.dim * q + a] = (int32_t)ddi::fine_start(t.k[d.dim * q + a], t.h[a], 2 * d.n[a], w);
+  }
+  return DDI_OK;
+}
+
+int ddi_plan_create(ddi_plan* out, const ddi_plan_desc* desc, void* stream) {
+  if (!out) {
+    ddi::set_error("out is NULL");
+    return DDI_ERR_ARG;
+  }
+  *out = nullptr;
+  ddi_plan_s* h = new (std::nothrow) ddi_plan_s();
+  if (!h) {
+    ddi::set_error("host allocation failed");
+    return DDI_ERR_OOM;
+  }
+  int s = ddi::create_plan(h->p, desc, static_cast<cudaStream_t>(stream));
+  if (s != DDI_OK) {
+    ddi::destroy_plan(h->p);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return DDI_OK;
+}
+
+int ddi_plan_destroy(ddi_plan plan) {
+  if (!plan) return DDI_OK;
+  ddi::destroy_plan(plan->p);
+  delete plan;
+  return DDI_OK;
+}
+
+int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info) {
+  if (!plan || !info) {
+    ddi::set_error("plan and info must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  const Plan& p = plan->p;
+  info->dim = p.dim;
+  info->precision = p.prec;
+  for (int a = 0; a < 3; ++a) {
+    info->n[a] = p.n[a];
+    info->nf[a] = p.nf[a];
+    info->tile[a] = p.tile[a];
+  }
+  info->width = p.w;
+  info->beta = p.beta;
+  info->nodes = p.M;
+  info->nodes_used = p.Mh;
+  info->spread_items = p.nitems;
+  info->spread_split_tiles = p.nsplit;
+  info->interp_items = (int)((p.Mh + 255) / 256);
+  info->kmax = p.desc.kmax;
+  info->nr = p.desc.nr;
+  info->ntheta = p.desc.ntheta;
+  info->nphi = p.desc.nphi;
+  info->device_bytes = p.bytes;
+  return DDI_OK;
+}
+
+int ddi_plan_node_order(ddi_plan plan, int64_t* q) {
+  if (!plan || !q) {
+    ddi::set_error("plan and q must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  memcpy(q, plan->p.order.data(), sizeof(int64_t) * plan->p.order.size());
+  return DDI_OK;
+}
+
+static int check_plan_ptrs(ddi_plan plan, const void* a, const void* b) {
+  if (!plan || !a || !b) {
+    ddi::set_error("plan and array pointers must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->p.device) {
+    ddi::set_error("the current device (%d) is not the plan's device (%d)", dev, plan->p.device);
+    return DDI_ERR_ARG;
+  }
+  return DDI_OK;
+}
+
+int ddi_apply(ddi_plan plan, const void* rho, void* phi, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, rho, phi));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  if (p.prec == DDI_FP64) return ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s);
+  return ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+}
+
+int ddi_apply_host(ddi_plan plan, const void* rho_host, void* phi_host, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, rho_host, phi_host));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  const size_t bytes = p.real_size() * (size_t)p.grid_points();
+  DDI_CUDA(cudaMemcpyAsync(p.d_io_in, rho_host, bytes, cudaMemcpyHostToDevice, s));
+  if (p.prec == DDI_FP64) {
+    DDI_TRY(ddi::run_ddi<double>(p, static_cast<const double*>(p.d_io_in), static_cast<double*>(p.d_io_out), s));
+  } else {
+    DDI_TRY(ddi::run_ddi<float>(p, static_cast<const float*>(p.d_io_in), static_cast<float*>(p.d_io_out), s));
+  }
+  DDI_CUDA(cudaMemcpyAsync(phi_host, p.d_io_out, bytes, cudaMemcpyDeviceToHost, s));
+  DDI_CUDA(cudaStreamSynchronize(s));
+  return DDI_OK;
+}
+
+int ddi_apply_timed(ddi_plan plan, const void* rho, void* phi, void* stream, const char** names, double* ms,
+                    int cap, int* count) {
+  DDI_TRY(check_plan_ptrs(plan, rho, phi));
+  if (!names || !ms || !count || cap < 1) {
+    ddi::set_error("names, ms and count must not be NULL and cap >= 1");
+    return DDI_ERR_ARG;
+  }
+  Plan& p = plan->p;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p.ev_created) {
+    for (cudaEvent_t& e : p.mark_ev) DDI_CUDA(cudaEventCreate(&e));
+    p.ev_created = true;
+  }
+  p.timing = true;
+  p.nmarks = 0;
+  DDI_CUDA(cudaEventRecord(p.mark_ev[0], s));
+  int st = p.prec == DDI_FP64
+               ? ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s)
+               : ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+  p.timing = false;
+  if (st != DDI_OK) return st;
+  DDI_CUDA(cudaStreamSynchronize(s));
+  const int n = p.nmarks < cap ? p.nmarks : cap;
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    DDI_CUDA(cudaEventElapsedTime(&t, p.mark_ev[i], p.mark_ev[i + 1]));
+    names[i] = p.mark_names[i];
+    ms[i] = (double)t;
+  }
+  *count = n;
+  return DDI_OK;
+}
+
+int ddi_type2(ddi_plan plan, const void* rho, void* c, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, rho, c));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  if (p.prec == DDI_FP64) {
+    DDI_TRY(ddi::run_type2<double>(p, static_cast<const double*>(rho), s));
+  } else {
+    DDI_TRY(ddi::run_type2<float>(p, static_cast<const float*>(rho), s));
+  }
+  DDI_CUDA(cudaMemcpyAsync(c, p.d_c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
+  return DDI_OK;
+}
+
+int ddi_type1(ddi_plan plan, const void* c, void* phi, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, c, phi));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  DDI_CUDA(cudaMemcpyAsync(p.d_c, c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
+  if (p.prec == DDI_FP64) return ddi::run_type1<double>(p, static_cast<double*>(phi), s);
+  return ddi::run_type1<float>(p, static_cast<float*>(phi), s);
+}
+
+}  // extern "C"

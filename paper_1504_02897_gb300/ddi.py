@@ -1,0 +1,342 @@
+"""Thin ctypes binding of ``libddi_gb300.so`` (declared in ``include/ddi.h``).
+
+Argument marshalling only: every step of the DDI / GPE path runs in the CUDA library.
+Device arrays are torch tensors on the plan's device, C-contiguous, shaped
+(nz, ny, nx) in 3D or (ny, nx) in 2D; real arrays are float64 (FP64 plans) or float32
+(FP32 plans), complex arrays complex128 / complex64.  Loading raises if the library has
+not been built (``python -c "import __graft_entry__ as g; g.build()"``): there is no
+fallback.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64 = 0
+FP32 = 1
+STOP_ENERGY = 0
+STOP_PAPER = 1
+
+_STATUS = {0: "DDI_OK", -1: "DDI_ERR_ARG", -2: "DDI_ERR_CUDA", -3: "DDI_ERR_OOM",
+           -4: "DDI_ERR_NONFINITE", -5: "DDI_ERR_TIMEOUT", -6: "DDI_ERR_NOCONV"}
+
+
+class DDIError(RuntimeError):
+    def __init__(self, status, where, message):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("len", ctypes.c_double * 3), ("axis_n", ctypes.c_double * 3), ("axis_m", ctypes.c_double * 3),
+                ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
+                ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
+                ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("precision", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("nf", ctypes.c_int * 3), ("width", ctypes.c_int), ("beta", ctypes.c_double),
+                ("nodes", ctypes.c_int64), ("nodes_used", ctypes.c_int64), ("tile", ctypes.c_int * 3),
+                ("spread_items", ctypes.c_int), ("spread_split_tiles", ctypes.c_int),
+                ("interp_items", ctypes.c_int), ("kmax", ctypes.c_double), ("nr", ctypes.c_int),
+                ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
+class GpeStats(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("mu", ctypes.c_double), ("Ekin", ctypes.c_double),
+                ("Epot", ctypes.c_double), ("Eint", ctypes.c_double), ("Edip", ctypes.c_double),
+                ("virial", ctypes.c_double), ("mass", ctypes.c_double), ("steps", ctypes.c_int),
+                ("inner_max", ctypes.c_int), ("last_change", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_plan_create", "ddi_plan_destroy",
+           "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
+           "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint"]
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load():
+    """Load the library (once).  Raises if it is missing: there is no CPU fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, cd, ci = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    sig = {
+        "ddi_status_str": ([ci], ctypes.c_char_p),
+        "ddi_last_error": ([], ctypes.c_char_p),
+        "ddi_quadrature_tables": ([ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_int64), vp, vp, vp], ci),
+        "ddi_plan_create": ([ctypes.POINTER(vp), ctypes.POINTER(PlanDesc), vp], ci),
+        "ddi_plan_destroy": ([vp], ci),
+        "ddi_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], ci),
+        "ddi_apply": ([vp, vp, vp, vp], ci),
+        "ddi_apply_host": ([vp, vp, vp, vp], ci),
+        "ddi_apply_timed": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(cd), ci,
+                             ctypes.POINTER(ci)], ci),
+        "ddi_type2": ([vp, vp, vp, vp], ci),
+        "ddi_type1": ([vp, vp, vp, vp], ci),
+        "ddi_plan_node_order": ([vp, vp], ci),
+        "gpe_step": ([vp, vp, vp, cd, cd, cd, ci, vp], ci),
+        "gpe_energy": ([vp, vp, vp, cd, cd, ctypes.POINTER(GpeStats), vp], ci),
+        "gpe_ground_state": ([vp, vp, vp, cd, cd, cd, cd, ci, cd, ci, ci, ctypes.POINTER(GpeStats), vp], ci),
+        "gpe_step_adjoint": ([vp, vp, vp, vp, vp, cd, cd, cd, vp], ci),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != 0:
+        msg = load().ddi_last_error().decode(errors="replace")
+        raise DDIError(status, where, msg)
+
+
+def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
+              precision=FP64, nufft_tol=0.0, tile=None, chunk=0):
+    d = PlanDesc()
+    d.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    lo3 = list(lo) + [0.0] * (3 - len(lo))
+    ln3 = list(length) + [1.0] * (3 - len(length))
+    for a in range(3):
+        d.n[a] = int(nn[a])
+        d.lo[a] = float(lo3[a])
+        d.len[a] = float(ln3[a])
+        d.axis_n[a] = float(axis_n[a])
+        d.axis_m[a] = float(axis_m[a]) if axis_m is not None else 0.0
+        d.tile[a] = int(tile[a]) if tile is not None else 0
+    d.nr, d.ntheta, d.nphi = int(nr), int(ntheta), int(nphi)
+    d.kmax = float(kmax)
+    d.precision = int(precision)
+    d.nufft_tol = float(nufft_tol)
+    d.chunk = int(chunk)
+    return d
+
+
+def quadrature_tables(desc):
+    """(k [M, dim], W [M], l0 [M, dim]) from the library's host plan builder (no GPU)."""
+    lib = load()
+    M = ctypes.c_int64(0)
+    _check(lib.ddi_quadrature_tables(ctypes.byref(desc), ctypes.byref(M), None, None, None), "quadrature_tables")
+    m = M.value
+    k = np.empty((m, desc.dim), dtype=np.float64)
+    W = np.empty(m, dtype=np.float64)
+    l0 = np.empty((m, desc.dim), dtype=np.int32)
+    _check(lib.ddi_quadrature_tables(ctypes.byref(desc), ctypes.byref(M), k.ctypes.data, W.ctypes.data,
+                                     l0.ctypes.data), "quadrature_tables")
+    return k, W, l0
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A DDI plan (quadrature, NUFFT tables, work lists and device workspace)."""
+
+    def __init__(self, dim, n, lo, length, axis_n, axis_m=None, precision=FP64, stream=None, **kw):
+        import torch
+        lib = load()
+        self.desc = make_desc(dim, n, lo, length, axis_n, axis_m, precision=precision, **kw)
+        self.dim = dim
+        self.precision = precision
+        self.shape = tuple(reversed(list(n)[:dim]))
+        self.real_dtype = torch.float64 if precision == FP64 else torch.float32
+        self.cplx_dtype = torch.complex128 if precision == FP64 else torch.complex64
+        h = ctypes.c_void_p()
+        _check(lib.ddi_plan_create(ctypes.byref(h), ctypes.byref(self.desc), ctypes.c_void_p(_stream(stream))),
+               "ddi_plan_create")
+        self._h = h
+        self.info = PlanInfo()
+        _check(lib.ddi_plan_get_info(self._h, ctypes.byref(self.info)), "ddi_plan_get_info")
+        self.dv = float(np.prod([length[d] / n[d] for d in range(dim)]))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ddi_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _req(self, t, complex_=False):
+        dt = self.cplx_dtype if complex_ else self.real_dtype
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != self.shape:
+            raise ValueError(f"expected a contiguous CUDA tensor of dtype {dt} and shape {self.shape}, got "
+                             f"{t.dtype} {tuple(t.shape)} on {t.device}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def apply(self, rho, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(rho)
+        _check(load().ddi_apply(self._h, self._req(rho), self._req(out), ctypes.c_void_p(_stream(stream))),
+               "ddi_apply")
+        return out
+
+    def apply_host(self, rho_host, out_host, stream=None):
+        """End-to-end from host (numpy or pinned torch CPU) buffers; synchronises."""
+        def ptr(a):
+            return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+        _check(load().ddi_apply_host(self._h, ptr(rho_host), ptr(out_host), ctypes.c_void_p(_stream(stream))),
+               "ddi_apply_host")
+        return out_host
+
+    def apply_timed(self, rho, out=None, stream=None):
+        """ddi_apply with per-launch CUDA-event times: returns (out, [(kernel, ms), ...])."""
+        import torch
+        if out is None:
+            out = torch.empty_like(rho)
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        cnt = ctypes.c_int(0)
+        _check(load().ddi_apply_timed(self._h, self._req(rho), self._req(out), ctypes.c_void_p(_stream(stream)),
+                                      names, ms, cap, ctypes.byref(cnt)), "ddi_apply_timed")
+        return out, [(names[i].decode(), ms[i]) for i in range(cnt.value)]
+
+    def type2(self, rho, stream=None):
+        import torch
+        c = torch.empty(int(self.info.nodes_used), dtype=self.cplx_dtype, device=rho.device)
+        _check(load().ddi_type2(self._h, self._req(rho), ctypes.c_void_p(c.data_ptr()),
+                                ctypes.c_void_p(_stream(stream))), "ddi_type2")
+        return c
+
+    def type1(self, c, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.real_dtype, device=c.device)
+        if c.dtype != self.cplx_dtype or c.numel() != int(self.info.nodes_used) or not c.is_contiguous():
+            raise ValueError("c must hold nodes_used contiguous complex values of the plan precision")
+        _check(load().ddi_type1(self._h, ctypes.c_void_p(c.data_ptr()), self._req(out),
+                                ctypes.c_void_p(_stream(stream))), "ddi_type1")
+        return out
+
+    def node_order(self):
+        q = np.empty(int(self.info.nodes_used), dtype=np.int64)
+        _check(load().ddi_plan_node_order(self._h, ctypes.c_void_p(q.ctypes.data)), "ddi_plan_node_order")
+        return q
+
+    # ---- GPE ----
+    def gpe_step(self, psi, V, beta, lam, dt, nsteps=1, stream=None):
+        _check(load().gpe_step(self._h, self._req(psi, True), self._req(V), float(beta), float(lam), float(dt),
+                               int(nsteps), ctypes.c_void_p(_stream(stream))), "gpe_step")
+        return psi
+
+    def gpe_energy(self, psi, V, beta, lam, stream=None):
+        st = GpeStats()
+        _check(load().gpe_energy(self._h, self._req(psi, True), self._req(V), float(beta), float(lam),
+                                 ctypes.byref(st), ctypes.c_void_p(_stream(stream))), "gpe_energy")
+        return st.as_dict()
+
+    def ground_state(self, phi, V, beta, lam, dt, tol, rule=STOP_ENERGY, inner_tol=None, max_steps=100000,
+                     check_every=1, stream=None):
+        if inner_tol is None:
+            inner_tol = 1e-13 if self.precision == FP64 else 1e-7
+        st = GpeStats()
+        status = load().gpe_ground_state(self._h, self._req(phi, True), self._req(V), float(beta), float(lam),
+                                         float(dt), float(tol), int(rule), float(inner_tol), int(max_steps),
+                                         int(check_every), ctypes.byref(st), ctypes.c_void_p(_stream(stream)))
+        if status not in (0, -6):
+            _check(status, "gpe_ground_state")
+        out = st.as_dict()
+        out["converged"] = status == 0
+        return out
+
+    def step_adjoint(self, psi_in, cot, grad_V, V, beta, lam, dt, stream=None):
+        _check(load().gpe_step_adjoint(self._h, self._req(psi_in, True), self._req(cot, True), self._req(grad_V),
+                                       self._req(V), float(beta), float(lam), float(dt),
+                                       ctypes.c_void_p(_stream(stream))), "gpe_step_adjoint")
+        return cot
+
+
+def trap_gradient(plan, psi0, V, beta, lam, dt, nsteps, checkpoint=20, stream=None):
+    """J = h^d sum z^2 |psi_T|^2 after nsteps TSFP steps and dJ/dV (hand-written adjoint).
+
+    Forward states are kept every ``checkpoint`` steps; the backward sweep recomputes
+    each segment's step inputs from its checkpoint, then applies the per-step adjoint
+    in reverse.  Returns (J, grad_V) as (float, tensor).
+    """
+    import torch
+    psi = psi0.clone()
+    ckpt = {0: psi.clone()}
+    for s in range(nsteps):
+        plan.gpe_step(psi, V, beta, lam, dt, 1, stream)
+        if (s + 1) % checkpoint == 0 and s + 1 < nsteps:
+            ckpt[s + 1] = psi.clone()
+    z = _z_coordinate(plan, psi.device)
+    J = plan.dv * float(torch.sum(z * z * (psi.real ** 2 + psi.imag ** 2)).item())
+    cot = (2.0 * z * z).to(psi.dtype) * psi
+    grad = torch.zeros_like(V)
+    seg_starts = sorted(ckpt.keys())
+    for start in reversed(seg_starts):
+        end = min(start + checkpoint, nsteps)
+        states = [ckpt[start].clone()]
+        cur = ckpt[start].clone()
+        for _ in range(start, end - 1):
+            plan.gpe_step(cur, V, beta, lam, dt, 1, stream)
+            states.append(cur.clone())
+        for k in range(end - start - 1, -1, -1):
+            plan.step_adjoint(states[k], cot, grad, V, beta, lam, dt, stream)
+    return J, grad
+
+
+def _z_coordinate(plan, device):
+    import torch
+    d = plan.desc
+    ax = plan.dim - 1
+    n = d.n[ax]
+    z = d.lo[ax] + torch.arange(n, dtype=torch.float64, device=device) * (d.len[ax] / n)
+    shape = [1] * plan.dim
+    shape[0] = n
+    return z.reshape(shape).to(plan.real_dtype)
+
+
+class TrapGradient:
+    """torch.autograd.Function-style wrapper: J(V) with backward through the adjoint."""
+
+    @staticmethod
+    def apply(plan, psi0, V, beta, lam, dt, nsteps, checkpoint=20):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Vt):
+                J, g = trap_gradient(plan, psi0, Vt.detach(), beta, lam, dt, nsteps, checkpoint)
+                ctx.save_for_backward(g)
+                return torch.tensor(J, dtype=torch.float64, device=Vt.device)
+
+            @staticmethod
+            def backward(ctx, gout):
+                (g,) = ctx.saved_tensors
+                return gout.to(g.dtype) * g
+
+        return _Fn.apply(V)

@@ -1,0 +1,202 @@
+"""GPU parity of the DDI path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L-infinity, normalised by max |oracle|): 1e-12 for FP64 plans,
+1e-6 for FP32 plans.  Full-size 128^3 checks compare the type-2 stage on sampled nodes
+and the type-1 stage (on seeded random node values) at sampled grid points, each
+against the oracle's per-node / per-point sums, in the plan bench.py times."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nudft
+from oracle import quadrature as qd
+from paper_1504_02897_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    ddi.load()
+    torch.cuda.init()
+    return ddi
+
+
+def _relinf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _plan(D, dim, n, lo, ln, axis, m=None, precision=0, **kw):
+    return D.Plan(dim, n, lo, ln, axis, m, precision=precision, **kw)
+
+
+def _run(D, plan, rho_np):
+    import torch
+    rho = torch.from_numpy(np.ascontiguousarray(rho_np)).to("cuda", plan.real_dtype)
+    out = plan.apply(rho)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+def _oracle(rho, n, lo, ln, axis, m=None, sizes=(0, 0, 0), dim=3):
+    t = qd.plan_tables(dim, n, ln, axis, m, nr=sizes[0], ntheta=sizes[1], nphi=sizes[2])
+    return nudft.ddi(rho, t, n, lo, ln)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ddi_anisotropic_gaussian_24(D, precision):
+    # 24^3 on [-6,6)^3, 16 x 16 x 32 rule, n = z (the closed-form case): parity with the sum
+    w = synth.anisotropic_gaussian_density(24, 6.0)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=16, ntheta=16, nphi=32)
+    got = _run(D, plan, w["rho"])
+    ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(16, 16, 32))
+    assert _relinf(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ddi_mixture_tilted_48(D, precision):
+    # several tiles and split (hot) tiles: 48^3, 8-Gaussian mixture, n = (sin 30, 0, cos 30)
+    w = synth.gaussian_mixture_density(48, 8.0, seed=1)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=48, ntheta=24, nphi=48)
+    assert plan.info.spread_split_tiles > 0
+    got = _run(D, plan, w["rho"])
+    ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(48, 24, 48))
+    assert _relinf(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ddi_ragged_anisotropic_box_two_axes(D, precision):
+    # unequal sizes and spacings per axis, box not centred, two dipole axes n != m
+    n, lo, ln = (32, 16, 24), (-3.0, -1.0, -5.0), (7.0, 3.0, 9.0)
+    rng = np.random.default_rng(11)
+    X, Y, Z = synth.coords(n, lo, ln)
+    rho = np.exp(-((X - 0.3) ** 2 / 1.5 + (Y + 0.2) ** 2 / 0.7 + (Z - 0.5) ** 2 / 2.0)) * (1 + 0.1 * rng.random(X.shape))
+    a = np.array([0.82778, 0.41505, -0.37751]); a /= np.linalg.norm(a)
+    b = np.array([0.31180, 0.93780, -0.15214]); b /= np.linalg.norm(b)
+    plan = _plan(D, 3, n, lo, ln, a, b, precision=precision, nr=20, ntheta=12, nphi=28)
+    got = _run(D, plan, rho)
+    ref = _oracle(rho, n, lo, ln, a, b, sizes=(20, 12, 28))
+    assert _relinf(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ddi_smallest_grid(D, precision):
+    n, lo, ln = (8, 8, 8), (-2.0, -2.0, -2.0), (4.0, 4.0, 4.0)
+    rho = np.random.default_rng(3).random((8, 8, 8))
+    plan = _plan(D, 3, n, lo, ln, (0, 0, 1), precision=precision)
+    got = _run(D, plan, rho)
+    ref = _oracle(rho, n, lo, ln, (0, 0, 1))
+    assert _relinf(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ddi_2d_polar(D, precision):
+    setup_n = np.array([0, -0.896, 0.44404])
+    setup_m = np.array([0, -0.52476, 0.85125])
+    n, lo, ln = (64, 48), (-8.0, -6.0), (16.0, 12.0)
+    X, Y = synth.coords(n, lo, ln)
+    rho = np.exp(-(X ** 2 + Y ** 2) / 1.3) + 0.5 * np.exp(-((X - 2) ** 2 + (Y + 1) ** 2))
+    plan = _plan(D, 2, n, lo, ln, setup_n, setup_m, precision=precision)
+    got = _run(D, plan, rho)
+    ref = _oracle(rho, n, lo, ln, setup_n, setup_m, dim=2)
+    assert _relinf(got, ref) <= TOL[precision]
+
+
+def test_ddi_zero_density_and_linearity(D):
+    import torch
+    n, lo, ln = (16, 16, 16), (-4.0,) * 3, (8.0,) * 3
+    plan = _plan(D, 3, n, lo, ln, (0.5, 0, math.sqrt(0.75)))
+    z = torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda")
+    assert float(plan.apply(z).abs().max()) == 0.0
+    rng = np.random.default_rng(5)
+    a = torch.from_numpy(rng.random((16, 16, 16))).cuda()
+    b = torch.from_numpy(rng.random((16, 16, 16))).cuda()
+    pa, pb, pab = plan.apply(a), plan.apply(b), plan.apply(2 * a - 3 * b)
+    assert float((pab - (2 * pa - 3 * pb)).abs().max() / pab.abs().max()) <= 1e-13
+
+
+def test_ddi_in_place_and_host_path(D):
+    import torch
+    w = synth.gaussian_mixture_density(32, 6.0, seed=2)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=1)
+    rho = torch.from_numpy(w["rho"]).to("cuda", torch.float32)
+    ref = plan.apply(rho).cpu().numpy()
+    host_in = torch.from_numpy(w["rho"].astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    plan.apply_host(host_in, host_out)
+    assert np.max(np.abs(host_out.numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
+    plan.apply(rho, out=rho)          # rho and phi may alias
+    torch.cuda.synchronize()
+    assert np.max(np.abs(rho.cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_nonunit_axis_rejected(D):
+    with pytest.raises(D.DDIError):
+        D.Plan(3, (16, 16, 16), (-1,) * 3, (2,) * 3, (0, 0, 2))
+
+
+def _config2(precision):
+    return synth.gaussian_mixture_density(128, 12.0, seed=0), dict(nr=128, ntheta=64, nphi=128)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_type2_sampled_nodes(D, precision):
+    # 128^3, 128 x 64 x 128 rule (~1M nodes): c_q = 2 h^3 W_q f_q at 3000 sampled nodes
+    import torch
+    w, sizes = _config2(precision)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, **sizes)
+    rho = torch.from_numpy(w["rho"]).to("cuda", plan.real_dtype)
+    c = plan.type2(rho).cpu().numpy().astype(np.complex128)
+    order = plan.node_order()
+    t = qd.plan_tables(3, w["n"], w["len"], w["axis"], nr=128, ntheta=64, nphi=128)
+    sel = np.random.default_rng(0).choice(len(order), 3000, replace=False)
+    q = order[sel]
+    k = t["k"][q]
+    rh = nudft.type2(w["rho"], k, w["n"], w["lo"], w["len"])
+    centre = np.array([w["lo"][d] + w["len"][d] / 2 for d in range(3)])
+    ref = 2.0 * t["W"][q] * rh * np.exp(1j * (k @ centre))
+    err = np.max(np.abs(c[sel] - ref)) / np.max(np.abs(ref))
+    assert err <= TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_type1_sampled_points(D, precision):
+    import torch
+    w, sizes = _config2(precision)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, **sizes)
+    mh = int(plan.info.nodes_used)
+    rng = np.random.default_rng(1)
+    c = (rng.standard_normal(mh) + 1j * rng.standard_normal(mh)) * 1e-3
+    ct = torch.from_numpy(c).to("cuda", plan.cplx_dtype)
+    phi = plan.type1(ct).double().cpu().numpy()
+    order = plan.node_order()
+    t = qd.plan_tables(3, w["n"], w["len"], w["axis"], nr=128, ntheta=64, nphi=128)
+    k = t["k"][order]
+    centre = np.array([w["lo"][d] + w["len"][d] / 2 for d in range(3)])
+    idx = rng.integers(0, 128, size=(400, 3))
+    pts = np.stack([w["lo"][d] + idx[:, d] * (w["len"][d] / 128) for d in range(3)], axis=1)
+    cin = c.astype(np.complex64).astype(np.complex128) if precision else c
+    ref = nudft.type1_at(cin * np.exp(-1j * (k @ centre)), k, pts)
+    got = phi[idx[:, 2], idx[:, 1], idx[:, 0]]
+    assert _relinf(got, ref) <= TOL[precision]
+
+
+def test_full_size_trace_identity(D):
+    # Phi_x + Phi_y + Phi_z = 0 for any rho (symbols sum to zero), at the full size
+    import torch
+    w, sizes = _config2(1)
+    tot = None
+    mx = 0.0
+    for e in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        plan = _plan(D, 3, w["n"], w["lo"], w["len"], e, precision=0, **sizes)
+        phi = plan.apply(torch.from_numpy(w["rho"]).cuda())
+        mx = max(mx, float(phi.abs().max()))
+        tot = phi if tot is None else tot + phi
+        del plan
+    assert float(tot.abs().max()) <= 1e-12 * mx

@@ -1,0 +1,139 @@
+"""GPU parity of the GPE layer (TSFP step, energies, gradient flow, adjoint) against the
+FP64 oracle, plus the paper's printed ground-state energies (Table virial_dip3d)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gpe as ogpe
+from oracle import nudft
+from oracle import quadrature as qd
+from paper_1504_02897_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    ddi.load()
+    return ddi
+
+
+def _setup(N, L, axis=(0.5, 0.0, math.sqrt(0.75)), gam=(1, 1, 2)):
+    n, lo, ln = synth.box(N, L)
+    grid = ogpe.Grid(n, lo, ln)
+    t = qd.plan_tables(3, n, ln, axis)
+    ddi = lambda rho: nudft.ddi(rho, t, n, lo, ln)
+    V = synth.harmonic_trap(n, lo, ln, gam)
+    psi0 = synth.gpe_initial(n, lo, ln, gam, eps=0.05, seed=3)
+    return n, lo, ln, grid, ddi, V, psi0
+
+
+def _t(x, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dtype)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+def test_tsfp_steps_match_oracle(D, precision, tol):
+    # FP32 tolerance: each step runs 2 FFT pairs of single-precision roundoff (~1e-7 per
+    # pass, growing with sqrt(log N) per transform) plus the 1e-6 DDI; 5 steps stay below 2e-5
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    beta, lam, dt, steps = 20.0, 8.0, 0.01, 5
+    ref = ogpe.tsfp_forward(grid, psi0, V, beta, lam, dt, steps, ddi)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=precision)
+    psi = _t(psi0, plan.cplx_dtype)
+    plan.gpe_step(psi, _t(V, plan.real_dtype), beta, lam, dt, steps)
+    got = psi.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_energies_match_oracle(D, precision, tol):
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    ref = ogpe.energies(grid, psi0, V, 30.0, 12.0, ddi)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=precision)
+    got = plan.gpe_energy(_t(psi0, plan.cplx_dtype), _t(V, plan.real_dtype), 30.0, 12.0)
+    for key in ("E", "mu", "Ekin", "Epot", "Eint", "Edip", "mass"):
+        assert abs(got[key] - ref[key]) <= tol * max(1.0, abs(ref[key])), (key, got[key], ref[key])
+
+
+def test_tsfp_mass_conservation_fp32_64(D):
+    import torch
+    n, lo, ln = synth.box(64, 8.0)
+    V = synth.harmonic_trap(n, lo, ln, (1, 1, 2))
+    psi0 = synth.gpe_initial(n, lo, ln, (1, 1, 2), eps=0.05, seed=4)
+    plan = D.Plan(3, n, lo, ln, (0.0, 0.0, 1.0), precision=1)
+    psi = _t(psi0, torch.complex64)
+    Vt = _t(V, torch.float32)
+    m0 = plan.gpe_energy(psi, Vt, 0.0, 0.0)["mass"]
+    plan.gpe_step(psi, Vt, 207.16, 33.1456, 1e-3, 100)
+    m1 = plan.gpe_energy(psi, Vt, 0.0, 0.0)["mass"]
+    assert abs(m1 - m0) <= 1e-5
+
+
+def test_gradient_flow_steps_match_oracle(D):
+    # max_steps = 4 with an unreachable tolerance: both sides take exactly 4 BE steps
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    phi0 = psi0.real.astype(np.complex128)
+    beta, lam, dt = 30.0, 12.0, 0.01
+    phi = phi0 / math.sqrt(ogpe.mass(grid, phi0))
+    for _ in range(4):
+        phi, _ = ogpe.gf_step(grid, phi, V, beta, lam, dt, ddi)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=0)
+    g = _t(phi0, plan.cplx_dtype)
+    st = plan.ground_state(g, _t(V, plan.real_dtype), beta, lam, dt, 1e-300, rule=D.STOP_PAPER, max_steps=4)
+    assert not st["converged"] and st["steps"] == 4
+    got = g.cpu().numpy()
+    assert np.max(np.abs(got - phi)) / np.max(np.abs(phi)) <= 1e-11
+
+
+def test_adjoint_matches_oracle_and_fd(D):
+    import torch
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    beta, lam, dt, steps = 15.0, 6.0, 0.01, 6
+    ref_grad, ref_J = ogpe.tsfp_adjoint(grid, psi0, V, beta, lam, dt, steps, ddi)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=0)
+    Vt = _t(V, torch.float64)
+    J, grad = D.trap_gradient(plan, _t(psi0, torch.complex128), Vt, beta, lam, dt, steps, checkpoint=4)
+    assert abs(J - ref_J) <= 1e-12 * abs(ref_J)
+    g = grad.cpu().numpy()
+    assert np.max(np.abs(g - ref_grad)) <= 1e-10 * np.max(np.abs(ref_grad))
+    # central differences of the GPU forward map
+    for d in synth.trap_directions(n, count=2, seed=9):
+        eps = 1e-4
+        vals = []
+        for sgn in (1, -1):
+            psi = _t(psi0, torch.complex128)
+            plan.gpe_step(psi, _t(V + sgn * eps * d, torch.float64), beta, lam, dt, steps)
+            vals.append(ogpe.observable_z2(grid, psi.cpu().numpy()))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        ad = float(np.sum(g * d))
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
+
+
+@pytest.mark.parametrize("row", [0, 2, 4])
+def test_virial_table_ground_state_energies(D, row):
+    # Table virial_dip3d (beta = 207.16, V = (x^2+y^2+z^2/4)/2, [-12,12]^3, h = 1/4, n = z):
+    # the GPU gradient flow reproduces the printed energies to their 5 significant figures.
+    import torch
+    tab = json.load(open(GOLDEN))["virial_dip3d"]
+    lam, E, mu, Ekin, Epot, Eint, Edip, I = tab["rows"][row]
+    n, lo, ln = synth.box(96, 12.0)
+    V = synth.harmonic_trap(n, lo, ln, (1, 1, 0.5))
+    phi0 = synth.gpe_initial(n, lo, ln, (1, 1, 0.5))
+    plan = D.Plan(3, n, lo, ln, (0.0, 0.0, 1.0), precision=0)
+    phi = _t(phi0, torch.complex128)
+    st = plan.ground_state(phi, _t(V, torch.float64), 207.16, lam, 0.01, 1e-12, rule=D.STOP_ENERGY,
+                           max_steps=20000, check_every=10)
+    assert st["converged"]
+    for got, want in ((st["E"], E), (st["mu"], mu), (st["Ekin"], Ekin), (st["Epot"], Epot), (st["Eint"], Eint)):
+        assert abs(got - want) <= 0.6 * 10 ** (math.floor(math.log10(abs(want))) - 4), (got, want)
+    if Edip != 0.0:
+        assert abs(st["Edip"] - Edip) <= 0.6 * 10 ** (math.floor(math.log10(abs(Edip))) - 4)
+    assert abs(st["virial"]) <= 1e-6

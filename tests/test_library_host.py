@@ -1,0 +1,102 @@
+"""Host-side checks of the CUDA library (no GPU needed): it builds, loads, exports every
+function include/ddi.h declares, and its host plan builder reproduces the oracle's
+quadrature tables bit for bit (same rule, same evaluation order, -ffp-contract=off)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import quadrature as qd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lib():
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    return ddi
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", txt, flags=re.M)
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    import ctypes
+    handle = ctypes.CDLL(lib.lib_path())
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(handle, name), name
+    assert set(lib.EXPORTS) <= set(declared)
+
+
+def test_status_strings(lib):
+    L = lib.load()
+    for s in (0, -1, -2, -3, -4, -5, -6):
+        assert L.ddi_status_str(s)
+
+
+CASES = [
+    dict(dim=3, n=(24, 24, 24), lo=(-6, -6, -6), length=(12, 12, 12), axis=(0, 0, 1), sizes=(16, 16, 32)),
+    dict(dim=3, n=(32, 16, 64), lo=(-4, -2, -8), length=(8, 3, 16), axis=(0.5, 0, math.sqrt(0.75)), sizes=(0, 0, 0)),
+    dict(dim=3, n=(128, 128, 128), lo=(-12,) * 3, length=(24,) * 3,
+         axis=(math.sin(math.radians(30)), 0, math.cos(math.radians(30))), sizes=(128, 64, 128)),
+    dict(dim=2, n=(256, 256), lo=(-10, -10), length=(20, 20), axis=(0.3, 0.0, math.sqrt(0.91)), sizes=(0, 0, 0)),
+    dict(dim=2, n=(64, 32), lo=(-8, -4), length=(16, 8), axis=(0, -0.896, 0.44404), m=(0, -0.52476, 0.85125),
+         sizes=(40, 0, 50)),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tables_bitwise_equal_oracle(lib, case, precision):
+    axis = np.array(case["axis"], float)
+    axis = axis / np.linalg.norm(axis)
+    m = case.get("m")
+    if m is not None:
+        m = np.array(m, float)
+        m = m / np.linalg.norm(m)
+    nr, nt, npp = case["sizes"]
+    desc = lib.make_desc(case["dim"], case["n"], case["lo"], case["length"], axis, m, nr=nr, ntheta=nt, nphi=npp,
+                         precision=precision)
+    k, W, l0 = lib.quadrature_tables(desc)
+    ref = qd.plan_tables(case["dim"], case["n"], case["length"], axis, m, nr=nr, ntheta=nt, nphi=npp)
+    assert k.shape == ref["k"].shape
+    assert np.array_equal(k, ref["k"]), np.max(np.abs(k - ref["k"]))
+    assert np.array_equal(W, ref["W"]), np.max(np.abs(W - ref["W"]))
+    width = {0: 14, 1: 8}[precision]
+    nf = [2 * v for v in case["n"]]
+    ref_l0 = qd.fine_grid_start(ref["k"], ref["h"], nf, width)
+    assert np.array_equal(l0.astype(np.int64), ref_l0)
+
+
+def test_gauss_legendre_bitwise_large(lib):
+    # 2D default radial rule at N = 1024 uses 2048 Gauss-Legendre nodes
+    desc = lib.make_desc(2, (1024, 1024), (-8, -8), (16, 16), (1, 0, 0), nr=2048, nphi=2)
+    k, W, _ = lib.quadrature_tables(desc)
+    ref = qd.plan_tables(2, (1024, 1024), (16, 16), (1, 0, 0), nr=2048, nphi=2)
+    assert np.array_equal(k, ref["k"]) and np.array_equal(W, ref["W"])
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(n=(20, 16, 16)), dict(n=(4, 16, 16)), dict(axis=(1, 1, 0)), dict(nphi=7),
+    dict(length=(0, 1, 1)), dict(precision=3),
+])
+def test_descriptor_validation(lib, bad):
+    args = dict(dim=3, n=(16, 16, 16), lo=(-1, -1, -1), length=(2, 2, 2), axis=(0, 0, 1), nphi=0, precision=0)
+    args.update(bad)
+    desc = lib.make_desc(args["dim"], args["n"], args["lo"], args["length"], args["axis"], nphi=args["nphi"],
+                         precision=args["precision"])
+    with pytest.raises(lib.DDIError) as e:
+        lib.quadrature_tables(desc)
+    assert e.value.status == -1
+    assert len(str(e.value)) > 20

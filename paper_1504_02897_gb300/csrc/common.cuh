@@ -89,6 +89,7 @@ struct Plan {
   int ntile[3] = {1, 1, 1};
   int nbins = 0;
   int chunk = 0;
+  int spread_method = 2;  // 1: warps own z-planes (no atomics), 2: shared-memory atomics
   int device = 0;
   size_t bytes = 0;
 

@@ -64,6 +64,14 @@ __global__ void k_phase_tables(cx_t<T>* tab, G3 g, double f) {
   }
 }
 
+// |e| = 1 restored after the product of the three rounded per-axis factors (FP32): a
+// fixed per-mode |e| != 1 would otherwise change the mass by the same amount every step
+__device__ __forceinline__ float2 unit_phase(float2 e) {
+  const float r = rsqrtf(e.x * e.x + e.y * e.y);
+  return make_float2(e.x * r, e.y * r);
+}
+__device__ __forceinline__ double2 unit_phase(double2 e) { return e; }
+
 // psihat <- psihat * e^{i f |mu|^2} / N_tot using the per-axis tables
 template <typename T>
 __global__ void k_kinetic(cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ tab, G3 g, T inv_n) {
@@ -76,7 +84,7 @@ __global__ void k_kinetic(cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ t
        i += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
     idx3(i, g, x, y, z);
-    const C f = cmul(cmul(tx[x], ty[y]), tz[z]);
+    const C f = unit_phase(cmul(cmul(tx[x], ty[y]), tz[z]));
     a[i] = cscale(cmul(a[i], f), inv_n);
   }
 }

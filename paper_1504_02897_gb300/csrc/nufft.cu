@@ -345,6 +345,199 @@ __global__ void __launch_bounds__(kThreads) k_spread(SpreadArgs a, T beta) {
   }
 }
 
+constexpr int kStageA = 128;  // nodes staged per round in k_spread_atomic
+
+// plane stride (in cells) of the padded accumulator: >= TY (TX + 1) and = 8 mod 32
+__host__ __device__ inline int atomic_plane_stride(int TX, int TY) {
+  const int ps = TY * (TX + 1);
+  return ps + (((8 - ps) % 32) + 32) % 32;
+}
+
+// Owner-computes spread with shared-memory atomics.  A CTA owns a fine-grid tile and
+// accumulates every node whose taps reach it.  The staged nodes are split into one
+// contiguous slice per warp; lanes own (z, y) rows of the w^d footprint and the w taps
+// of each row.  Nodes are sorted by first tap within each bin, so a run of nodes with
+// the same footprint (the k ~ 0 hot spot is made of such runs) accumulates in
+// registers (REG) and reaches shared memory once per run; rows outside the tile are
+// skipped.  Without REG (large widths) every node goes straight to shared memory.
+template <typename T, int W, int DIM, bool REG>
+__global__ void __launch_bounds__(kThreads) k_spread_atomic(SpreadArgs a, T beta) {
+  using C = cx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
+  const int cells = TX * TY * TZ;
+  // planar re / im accumulators with padded strides: row stride TX + 1 and a plane
+  // stride = 8 (mod 32), so the 32 rows a warp touches fall in 32 different banks
+  const int RS = TX + 1;
+  const int PS = atomic_plane_stride(TX, TY);
+  const int cellsP = TZ * PS;
+  T* acc = reinterpret_cast<T*>(smem_raw);                      // re [cellsP], im [cellsP]
+  C* cv = reinterpret_cast<C*>(acc + 2 * cellsP);               // [kStageA]
+  T* kv = reinterpret_cast<T*>(cv + kStageA);                   // [kStageA][3][W]
+  int* lv = reinterpret_cast<int*>(kv + kStageA * 3 * W);      // [kStageA][3]
+  __shared__ int nb_begin[8], nb_prefix[9];
+
+  const SpreadItem it = a.items[blockIdx.x];
+  const int tx = it.tile % a.ntile[0];
+  const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
+  const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
+  const int T0x = tx * TX, T0y = ty * TY, T0z = tz * TZ;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    nb_prefix[0] = 0;
+    for (int dz = 0; dz < (DIM == 3 && a.ntile[2] > 1 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < (a.ntile[1] > 1 ? 2 : 1); ++dy)
+        for (int dx = 0; dx < (a.ntile[0] > 1 ? 2 : 1); ++dx) {
+          const int bx = (tx - dx + a.ntile[0]) % a.ntile[0];
+          const int by = (ty - dy + a.ntile[1]) % a.ntile[1];
+          const int bz = (tz - dz + a.ntile[2]) % a.ntile[2];
+          const int b = (bz * a.ntile[1] + by) * a.ntile[0] + bx;
+          nb_begin[k] = a.bin_start[b];
+          nb_prefix[k + 1] = nb_prefix[k] + (a.bin_start[b + 1] - a.bin_start[b]);
+          ++k;
+        }
+    for (; k < 8; ++k) {
+      nb_begin[k] = 0;
+      nb_prefix[k + 1] = nb_prefix[k];
+    }
+  }
+  for (int i = threadIdx.x; i < 2 * cellsP; i += blockDim.x) acc[i] = (T)0;
+  __syncthreads();
+
+  const Pos4<T>* pos = static_cast<const Pos4<T>*>(a.pos);
+  const C* cin = static_cast<const C*>(a.c);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int ROWS = DIM == 3 ? W * W : W;   // (z, y) rows of one footprint
+  constexpr int RPL = (ROWS + 31) / 32;        // rows per lane
+  const int nfx = a.g.nf[0], nfy = a.g.nf[1], nfz = a.g.nf[2];
+
+  for (int v0 = it.vbeg; v0 < it.vend; v0 += kStageA) {
+    const int cnt = min(kStageA, it.vend - v0);
+    for (int j = threadIdx.x; j < 3 * cnt; j += blockDim.x) {
+      const int ax = j / cnt, k = j - ax * cnt;
+      if (DIM == 2 && ax == 2) continue;
+      const int v = v0 + k;
+      int b = 0;
+      while (v >= nb_prefix[b + 1]) ++b;
+      const int node = nb_begin[b] + (v - nb_prefix[b]);
+      const Pos4<T> pp = pos[node];
+      es_taps<T, W>(ax == 0 ? pp.x : (ax == 1 ? pp.y : pp.z), beta, kv + (k * 3 + ax) * W);
+      if (ax == 0) {
+        cv[k] = cin[node];
+        const ushort4 sl = a.l0[node];
+        lv[k * 3 + 0] = sl.x;
+        lv[k * 3 + 1] = sl.y;
+        lv[k * 3 + 2] = sl.z;
+      }
+    }
+    __syncthreads();
+    const int per = (cnt + kWarps - 1) / kWarps;
+    const int k0 = warp * per, k1 = min(cnt, k0 + per);
+    if (REG) {
+      T ar[RPL][W], ai[RPL][W];
+      int lz[RPL], ly[RPL];
+      int run = -1;
+#pragma unroll
+      for (int i = 0; i < RPL; ++i)
+#pragma unroll
+        for (int q = 0; q < W; ++q) ar[i][q] = ai[i][q] = (T)0;
+      for (int k = k0; k <= k1; ++k) {
+        const bool same = run >= 0 && k < k1 && lv[k * 3] == lv[run * 3] && lv[k * 3 + 1] == lv[run * 3 + 1] &&
+                          lv[k * 3 + 2] == lv[run * 3 + 2];
+        if (run >= 0 && !same) {
+          // flush the finished run into the tile (rows and taps outside it are dropped)
+          const int sx = lv[run * 3];
+#pragma unroll
+          for (int i = 0; i < RPL; ++i) {
+            if (lz[i] < TZ && ly[i] < TY) {
+              const int base = lz[i] * PS + ly[i] * RS;
+#pragma unroll
+              for (int q = 0; q < W; ++q) {
+                const int lx = wrap2(sx + q - T0x, nfx);
+                if (lx < TX) {
+                  atomicAdd(acc + base + lx, ar[i][q]);
+                  atomicAdd(acc + cellsP + base + lx, ai[i][q]);
+                }
+                ar[i][q] = ai[i][q] = (T)0;
+              }
+            }
+          }
+          run = -1;
+        }
+        if (k == k1) break;
+        if (run < 0) {
+          run = k;
+#pragma unroll
+          for (int i = 0; i < RPL; ++i) {
+            const int r = lane + 32 * i;
+            const int az = DIM == 3 ? r / W : 0, ay = DIM == 3 ? r - (r / W) * W : r;
+            const bool valid = r < ROWS;
+            lz[i] = valid ? (DIM == 3 ? wrap2(lv[k * 3 + 2] + az - T0z, nfz) : 0) : TZ;
+            ly[i] = valid ? wrap2(lv[k * 3 + 1] + ay - T0y, nfy) : TY;
+          }
+        }
+        const T* kk = kv + k * 3 * W;
+        const C cq = cv[k];
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          if (lz[i] < TZ && ly[i] < TY) {
+            const int r = lane + 32 * i;
+            const int az = DIM == 3 ? r / W : 0, ay = DIM == 3 ? r - (r / W) * W : r;
+            const T wzy = (DIM == 3 ? kk[2 * W + az] : (T)1) * kk[W + ay];
+            const T czr = cq.x * wzy, czi = cq.y * wzy;
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+              ar[i][q] += czr * kk[q];
+              ai[i][q] += czi * kk[q];
+            }
+          }
+        }
+      }
+    } else {
+      for (int k = k0; k < k1; ++k) {
+        const T* kk = kv + k * 3 * W;
+        const C cq = cv[k];
+        const int sx = lv[k * 3], sy = lv[k * 3 + 1], sz = lv[k * 3 + 2];
+        for (int r = lane; r < ROWS; r += 32) {
+          const int az = DIM == 3 ? r / W : 0, ay = DIM == 3 ? r - (r / W) * W : r;
+          const int z = DIM == 3 ? wrap2(sz + az - T0z, nfz) : 0;
+          const int y = wrap2(sy + ay - T0y, nfy);
+          if (z >= TZ || y >= TY) continue;
+          const T wzy = (DIM == 3 ? kk[2 * W + az] : (T)1) * kk[W + ay];
+          const T czr = cq.x * wzy, czi = cq.y * wzy;
+          const int base = z * PS + y * RS;
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            const int lx = wrap2(sx + q - T0x, nfx);
+            if (lx < TX) {
+              atomicAdd(acc + base + lx, czr * kk[q]);
+              atomicAdd(acc + cellsP + base + lx, czi * kk[q]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (it.slot < 0) {
+    C* fine = static_cast<C*>(a.fine);
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+      const int lx = i % TX, ly2 = (i / TX) % TY, lz2 = i / (TX * TY);
+      const long long off = ((long long)(T0z + lz2) * nfy + (T0y + ly2)) * nfx + (T0x + lx);
+      const int pi = lz2 * PS + ly2 * RS + lx;
+      fine[off] = cmk<C>(acc[pi], acc[cellsP + pi]);
+    }
+  } else {
+    C* part = static_cast<C*>(a.partial) + (long long)it.slot * cells;
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+      const int lx = i % TX, ly2 = (i / TX) % TY, lz2 = i / (TX * TY);
+      const int pi = lz2 * PS + ly2 * RS + lx;
+      part[i] = cmk<C>(acc[pi], acc[cellsP + pi]);
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __restrict__ partial,
                          cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx,
@@ -397,7 +590,10 @@ int launch_interp(const Plan& p, cudaStream_t s) {
 size_t spread_smem(const Plan& p) {
   const size_t cells = (size_t)p.tile[0] * p.tile[1] * p.tile[2];
   const size_t rs = p.real_size();
-  return cells * p.cx_size() + kStage * p.cx_size() + (size_t)kStage * 3 * p.w * rs + kStage * 3 * sizeof(int);
+  if (p.spread_method == 1)
+    return cells * p.cx_size() + kStage * p.cx_size() + (size_t)kStage * 3 * p.w * rs + kStage * 3 * sizeof(int);
+  const size_t cellsP = (size_t)p.tile[2] * atomic_plane_stride(p.tile[0], p.tile[1]);
+  return cellsP * p.cx_size() + kStageA * p.cx_size() + (size_t)kStageA * 3 * p.w * rs + kStageA * 3 * sizeof(int);
 }
 
 template <typename T, int W, int DIM>
@@ -416,7 +612,8 @@ int launch_spread(const Plan& p, cudaStream_t s) {
   a.fine = p.d_fine;
   a.partial = p.d_partial;
   const size_t smem = spread_smem(p);
-  auto kern = k_spread<T, W, DIM>;
+  auto kern = p.spread_method == 1 ? k_spread<T, W, DIM>
+                                   : (W <= 8 ? k_spread_atomic<T, W, DIM, true> : k_spread_atomic<T, W, DIM, false>);
   if (smem > 48 * 1024) {
     DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
@@ -577,13 +774,15 @@ void choose_tile(Plan& p) {
   const int need = p.w - 1;
   int want[3];
   if (p.dim == 3) {
-    if (p.prec == DDI_FP32) {
-      want[0] = 16; want[1] = 16; want[2] = 8;
+    if (p.spread_method == 1) {
+      want[0] = 16; want[1] = 16; want[2] = p.prec == DDI_FP32 ? 8 : 16;
+    } else if (p.prec == DDI_FP32) {
+      want[0] = 32; want[1] = 16; want[2] = 16;
     } else {
       want[0] = 16; want[1] = 16; want[2] = 16;
     }
   } else {
-    want[0] = 32; want[1] = 32; want[2] = 1;
+    want[0] = 64; want[1] = 32; want[2] = 1;
   }
   for (int d = 0; d < 3; ++d) {
     if (p.desc.tile[d] > 0) want[d] = p.desc.tile[d];
@@ -615,6 +814,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   }
   p.w = kernel_width(d);
   p.beta = kernel_beta(p.w);
+  p.spread_method = d.spread_method == 1 ? 1 : 2;
   build_quadrature(d, &p.quad);
   p.M = p.quad.M;
   choose_tile(p);
@@ -649,7 +849,13 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   p.nbins = p.ntile[0] * p.ntile[1] * p.ntile[2];
   std::vector<int64_t> perm(p.Mh);
   std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return bin[a] < bin[b]; });
+  // sort by bin, then by first tap so that nodes with one footprint are consecutive
+  std::vector<int64_t> key(p.Mh);
+  for (int64_t i = 0; i < p.Mh; ++i)
+    key[i] = ((int64_t)l0w[3 * i + 2] * p.nf[1] + l0w[3 * i + 1]) * p.nf[0] + l0w[3 * i];
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) {
+    return bin[a] != bin[b] ? bin[a] < bin[b] : key[a] < key[b];
+  });
   std::vector<int> bin_start(p.nbins + 1, 0);
   for (int64_t i = 0; i < p.Mh; ++i) bin_start[bin[i] + 1]++;
   for (int b = 0; b < p.nbins; ++b) bin_start[b + 1] += bin_start[b];

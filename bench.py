@@ -2,8 +2,10 @@
 with the HBM roofline of the dominant kernel, an end-to-end host-buffer number and the
 FP64 CPU oracle timed on this machine's cores.
 
-Workload (one step = one DDI, i.e. one pass of the whole hot path: pad, 3 forward FFT
-passes, interpolation x symbol x weights, spread, 3 inverse FFT passes, crop): 128^3 grid
+Workload (one step = one DDI, i.e. one pass of the whole hot path: type-2 NUFFT (pad and
+deconvolution fused into the first of 3 forward fine-grid FFT passes, interpolation at the
+nodes times symbol x quadrature weights), type-1 NUFFT (spread, 3 inverse FFT passes, the
+last fused with crop, deconvolution and real part)): 128^3 grid
 on [-12,12)^3, density a seeded sum of 8 anisotropic Gaussians (widths U[0.5,2], centres
 U[-4,4]^3), dipole axis n = (sin 30, 0, cos 30), quadrature 128 x 64 x 128 (1,048,576
 nodes), NUFFT tolerance 1e-6.  Rank r of a multi-GPU run evaluates the density with seed
@@ -170,21 +172,25 @@ def run_reference(args):
     }))
 
 
-# algorithmic bytes per launch of each kernel (FP32-mixed path, nf = 2N), see the design doc
+# Algorithmic bytes per launch of each kernel of the FP32 path (n = N^3 grid points,
+# fine grid 2N per axis, complex 8 B): each pass moves the data it must read and write
+# once; the padded / cropped passes touch only the block they need.
 def kernel_bytes(name, info, real=4):
     cx = 2 * real
     n3 = N ** 3
-    nf3 = (2 * N) ** 3
     mh = int(info.nodes_used)
     node_in = mh * (8 + 4 * real)          # ushort4 start taps + 4 reals (offsets, weight)
+    ball = int(4.0 / 3.0 * 3.141592653589793 * (N + info.width / 2.0) ** 3) * cx   # cells the taps reach
     table = {
-        "pad": n3 * real + nf3 * cx,
-        "fft_x_fwd": 2 * nf3 * cx, "fft_y_fwd": 2 * nf3 * cx, "fft_z_fwd": 2 * nf3 * cx,
-        "fft_x_inv": 2 * nf3 * cx, "fft_y_inv": 2 * nf3 * cx, "fft_z_inv": 2 * nf3 * cx,
-        "interp": nf3 * cx + node_in + mh * cx,
-        "spread": nf3 * cx + node_in + mh * cx,
+        "pad_fft_x": n3 * real + 2 * n3 * cx,           # read rho, write N^2 rows of 2N
+        "fft_y_fwd": 2 * n3 * cx + 4 * n3 * cx,         # read the block half, write planes
+        "fft_z_fwd": 4 * n3 * cx + 8 * n3 * cx,
+        "interp": ball + node_in + mh * cx,
+        "spread": 8 * n3 * cx + node_in + mh * cx,      # every fine cell written once
         "spread_reduce": 0,
-        "crop": n3 * cx + n3 * real,
+        "fft_z_inv": 8 * n3 * cx + 4 * n3 * cx,
+        "fft_y_inv": 4 * n3 * cx + 2 * n3 * cx,
+        "fft_x_inv_crop": 2 * n3 * cx + n3 * real,
     }
     return table.get(name, 0)
 

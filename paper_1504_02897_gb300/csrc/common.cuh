@@ -89,7 +89,7 @@ struct Plan {
   int ntile[3] = {1, 1, 1};
   int nbins = 0;
   int chunk = 0;
-  int spread_method = 2;  // 1: warps own z-planes (no atomics), 2: shared-memory atomics
+  int spread_method = 1;  // 1: warps own z-planes (no atomics), 2: shared-memory atomics
   int device = 0;
   size_t bytes = 0;
 
@@ -104,6 +104,8 @@ struct Plan {
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
   void* d_partial = nullptr;  // cx [nslots * tile cells]
   int* d_bin_start = nullptr; // [nbins + 1]
+  int* d_vlist = nullptr;     // spread visit lists (node indices), per tile
+  long long visits = 0;       // total list entries
   SpreadItem* d_items = nullptr;
   SplitTile* d_split = nullptr;
   int nitems = 0, nsplit = 0, nslots = 0;
@@ -155,6 +157,10 @@ int fft_axis(const Plan& p, cx_t<T>* data, int nx, int ny, int nz, int axis, int
 template <typename T>
 int fft_3d(const Plan& p, cx_t<T>* data, int nx, int ny, int nz, int dir, cudaStream_t s);
 int make_twiddles(Plan& p, int n);
+
+// ---- pruned / fused fine-grid FFTs of the NUFFT (fft_nufft.cu) ----------------------
+template <typename T> int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t s);  // rho -> F (fine grid)
+template <typename T> int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s);        // U (fine grid) -> phi
 
 // ---- NUFFT stages (nufft.cu) --------------------------------------------------------
 template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);       // rho -> d_c

@@ -14,16 +14,15 @@
 // with deconvolution by its Fourier transform psihat(2 pi j'/nf).
 //
 // Kernels (one launch each):
-//   k_pad        rho / psihat placed at j' mod nf, zero elsewhere      (type-2 prologue)
-//   fft (fft.cu) forward 3 passes
+//   fft_nufft.cu forward passes x (fused with the pad and deconvolution), y, z, pruned
+//                to the padded block
 //   k_interp     f_q = sum over the w^d taps of psi * F, times 2 h^d W_q (one thread per node)
-//   k_spread     owner-computes spread: a CTA owns a fine-grid tile, accumulates every
-//                node whose taps reach it in shared memory (warps own z-planes, so no
-//                atomics), and writes the tile once; tiles with more visits than one
-//                work item takes are split into partial tiles
+//   k_spread_planes  owner-computes spread: a CTA owns a fine-grid tile and its list of
+//                the nodes whose taps reach it; warps own z-planes, so no atomics; the
+//                tile is written once; long lists are split into partial tiles
 //   k_reduce     sums the partial tiles of split tiles
-//   fft          inverse 3 passes
-//   k_crop       Phi_j = Re U_{j' mod nf} / psihat
+//   fft_nufft.cu inverse passes z, y, x (pruned to the cropped block, the last fused
+//                with crop, deconvolution and real part)
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -52,7 +51,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kStage = 64;  // nodes staged per round in k_spread
 
 template <typename T> struct Pos4 { T x, y, z, w; };
 
@@ -82,68 +80,6 @@ struct GridDims {
 __device__ __forceinline__ int wrap1(int i, int nf) { return i >= nf ? i - nf : i; }
 // i in (-nf, 2 nf) -> i mod nf
 __device__ __forceinline__ int wrap2(int i, int nf) { return i < 0 ? i + nf : (i >= nf ? i - nf : i); }
-
-// ---- type-2 prologue -------------------------------------------------------------------
-template <typename T>
-__global__ void k_pad(const T* __restrict__ rho, cx_t<T>* __restrict__ fine,
-                      const T* __restrict__ dc, GridDims g) {
-  using C = cx_t<T>;
-  const long long total = (long long)g.nf[0] * g.nf[1] * g.nf[2];
-  const T* dcx = dc;
-  const T* dcy = dc + g.n[0];
-  const T* dcz = dcy + g.n[1];
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int lx = (int)(idx % g.nf[0]);
-    const long long r = idx / g.nf[0];
-    const int ly = (int)(r % g.nf[1]);
-    const int lz = (int)(r / g.nf[1]);
-    int j[3];
-    const int l[3] = {lx, ly, lz};
-    bool inside = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int hn = g.n[d] / 2;
-      if (g.n[d] == 1) {
-        j[d] = 0;
-      } else if (l[d] < hn) {
-        j[d] = l[d] + hn;
-      } else if (l[d] >= g.nf[d] - hn) {
-        j[d] = l[d] - g.nf[d] + hn;
-      } else {
-        inside = false;
-        j[d] = 0;
-      }
-    }
-    T v = (T)0;
-    if (inside) {
-      v = rho[((long long)j[2] * g.n[1] + j[1]) * g.n[0] + j[0]] * (dcx[j[0]] * dcy[j[1]] * dcz[j[2]]);
-    }
-    fine[idx] = cmk<C>(v, (T)0);
-  }
-}
-
-// ---- type-1 epilogue ---------------------------------------------------------------------
-template <typename T>
-__global__ void k_crop(const cx_t<T>* __restrict__ fine, T* __restrict__ phi,
-                       const T* __restrict__ dc, GridDims g) {
-  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  const T* dcx = dc;
-  const T* dcy = dc + g.n[0];
-  const T* dcz = dcy + g.n[1];
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int jx = (int)(idx % g.n[0]);
-    const long long r = idx / g.n[0];
-    const int jy = (int)(r % g.n[1]);
-    const int jz = (int)(r / g.n[1]);
-    const int lx = (jx - g.n[0] / 2 + g.nf[0]) % g.nf[0];
-    const int ly = (jy - g.n[1] / 2 + g.nf[1]) % g.nf[1];
-    const int lz = (jz - g.n[2] / 2 + g.nf[2]) % g.nf[2];
-    const T u = fine[((long long)lz * g.nf[1] + ly) * g.nf[0] + lx].x;
-    phi[idx] = u * (dcx[jx] * dcy[jy] * dcz[jz]);
-  }
-}
 
 // ---- interpolation (type 2) -----------------------------------------------------------------
 template <typename T, int W, int DIM>
@@ -209,7 +145,7 @@ struct SpreadArgs {
   int tile[3];
   int ntile[3];
   const SpreadItem* items;
-  const int* bin_start;
+  const int* vlist;  // per-tile visit lists: nodes whose taps reach the tile, by (oz, oy, ox)
   const ushort4* l0;
   const void* pos;
   const void* c;
@@ -217,131 +153,154 @@ struct SpreadArgs {
   void* partial;
 };
 
+// Start of a footprint relative to a tile origin: l0 - T0 wrapped into [-(w-1), nf-(w-1)),
+// so that footprints reaching the tile from below (through the periodic wrap) are negative.
+__host__ __device__ inline int rel_start(int l0, int T0, int nf, int w) {
+  int o = l0 - T0;
+  if (o < 0) o += nf;
+  if (o > nf - w) o -= nf;
+  return o;
+}
+// padded row stride (cells) of the plane-owned accumulator: = 8 (mod 16) so that the two
+// 8-cell row segments one half-warp touches fall in different halves of the banks
+__host__ __device__ inline int spread_row_stride(int TX) { return TX + ((8 - TX % 16) + 16) % 16; }
+
+constexpr int kStageS = 128;  // nodes staged per round in k_spread_planes
+
+// Plane-owned spread (no atomics).  A CTA owns a fine-grid tile; its visit list holds
+// exactly the nodes whose w^d taps reach the tile, sorted by relative start
+// (oz, oy, ox).  After staging a round of nodes (kernel values, c psi_z, starts), warp
+// `p mod 8` owns z-plane p of the tile: it binary-searches the staged nodes whose z taps
+// cover p, and its lanes (x fastest, then y rows) add c psi_z psi_y psi_x into the
+// plane's cells with plain shared-memory read-modify-writes: no other warp touches the
+// plane and a lane never meets the same cell twice in one node.  In 2D the owned unit
+// is a y-row.
 template <typename T, int W, int DIM>
-__global__ void __launch_bounds__(kThreads) k_spread(SpreadArgs a, T beta) {
+__global__ void __launch_bounds__(kThreads) k_spread_planes(SpreadArgs a, T beta) {
   using C = cx_t<T>;
+  constexpr int XL = W <= 8 ? 8 : 16;   // lanes along x
+  constexpr int RL = 32 / XL;           // y rows per warp instruction (3D)
+  constexpr int MR = (W + RL - 1) / RL; // row iterations per (node, plane)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
-  const int cells = TX * TY * TZ;
-  C* acc = reinterpret_cast<C*>(smem_raw);
-  C* cv = acc + cells;                                   // [kStage]
-  T* kv = reinterpret_cast<T*>(cv + kStage);             // [kStage][3][W]
-  int* lv = reinterpret_cast<int*>(kv + kStage * 3 * W); // [kStage][3]
-  __shared__ int nb_begin[8], nb_count[8], nb_prefix[9];
+  const int RS = spread_row_stride(TX);
+  const int NPL = DIM == 3 ? TZ : TY;          // owned units: z-planes (3D) or y-rows (2D)
+  const int PSZ = DIM == 3 ? TY * RS : RS;     // cells per owned unit
+  C* acc = reinterpret_cast<C*>(smem_raw);     // [NPL][PSZ]
+  C* cz = acc + NPL * PSZ;                     // [kStageS][W]: c psi_z (3D) / c psi_y (2D)
+  T* py = reinterpret_cast<T*>(cz + kStageS * W);  // [kStageS][W] (3D only)
+  T* px = py + kStageS * W;                    // [kStageS][W]
+  int* oo = reinterpret_cast<int*>(px + kStageS * W);  // [kStageS][4]: ox, oy, oz, plane key
 
   const SpreadItem it = a.items[blockIdx.x];
   const int tx = it.tile % a.ntile[0];
   const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
   const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
   const int T0x = tx * TX, T0y = ty * TY, T0z = tz * TZ;
-  if (threadIdx.x == 0) {
-    // visit list: own bin and the lower neighbours (offset 1 exists only with >= 2 tiles)
-    int k = 0;
-    nb_prefix[0] = 0;
-    for (int dz = 0; dz < (DIM == 3 && a.ntile[2] > 1 ? 2 : 1); ++dz)
-      for (int dy = 0; dy < (a.ntile[1] > 1 ? 2 : 1); ++dy)
-        for (int dx = 0; dx < (a.ntile[0] > 1 ? 2 : 1); ++dx) {
-          const int bx = (tx - dx + a.ntile[0]) % a.ntile[0];
-          const int by = (ty - dy + a.ntile[1]) % a.ntile[1];
-          const int bz = (tz - dz + a.ntile[2]) % a.ntile[2];
-          const int b = (bz * a.ntile[1] + by) * a.ntile[0] + bx;
-          nb_begin[k] = a.bin_start[b];
-          nb_count[k] = a.bin_start[b + 1] - a.bin_start[b];
-          nb_prefix[k + 1] = nb_prefix[k] + nb_count[k];
-          ++k;
-        }
-    for (; k < 8; ++k) {
-      nb_begin[k] = 0;
-      nb_count[k] = 0;
-      nb_prefix[k + 1] = nb_prefix[k];
-    }
-  }
-  for (int i = threadIdx.x; i < cells; i += blockDim.x) acc[i] = cmk<C>((T)0, (T)0);
-  __syncthreads();
+  const int nfx = a.g.nf[0], nfy = a.g.nf[1], nfz = a.g.nf[2];
+  const bool wrx = a.ntile[0] == 1, wry = a.ntile[1] == 1, wrz = a.ntile[2] == 1;
+  const bool wrp = DIM == 3 ? wrz : wry;       // owned axis wraps inside the tile
+  const int nfp = DIM == 3 ? nfz : nfy;
+
+  for (int i = threadIdx.x; i < NPL * PSZ; i += blockDim.x) acc[i] = cmk<C>((T)0, (T)0);
 
   const Pos4<T>* pos = static_cast<const Pos4<T>*>(a.pos);
   const C* cin = static_cast<const C*>(a.c);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rx = lane % XL, ry = lane / XL;
 
-  for (int v0 = it.vbeg; v0 < it.vend; v0 += kStage) {
-    const int cnt = min(kStage, it.vend - v0);
-    if (threadIdx.x < cnt) {
-      const int v = v0 + threadIdx.x;
-      int k = 0;
-      while (v >= nb_prefix[k + 1]) ++k;
-      const int node = nb_begin[k] + (v - nb_prefix[k]);
-      const ushort4 s = a.l0[node];
-      const Pos4<T> p = pos[node];
-      T* kk = kv + threadIdx.x * 3 * W;
-      es_taps<T, W>(p.x, beta, kk);
-      es_taps<T, W>(p.y, beta, kk + W);
-      if (DIM == 3) es_taps<T, W>(p.z, beta, kk + 2 * W);
-      cv[threadIdx.x] = cin[node];
-      lv[threadIdx.x * 3 + 0] = s.x;
-      lv[threadIdx.x * 3 + 1] = s.y;
-      lv[threadIdx.x * 3 + 2] = s.z;
-    }
-    __syncthreads();
-    for (int k = 0; k < cnt; ++k) {
-      const T* kk = kv + k * 3 * W;
-      const C cq = cv[k];
-      const int sx = lv[k * 3], sy = lv[k * 3 + 1], sz = lv[k * 3 + 2];
-      if (DIM == 3) {
-        // warp `warp` owns the local z-planes lz with lz % kWarps == warp
-        for (int az = 0; az < W; ++az) {
-          const int lz = wrap2(sz + az - T0z, a.g.nf[2]);
-          if (lz >= TZ || (lz % kWarps) != warp) continue;
-          const T wz = kk[2 * W + az];
-          const T czr = cq.x * wz, czi = cq.y * wz;
-          C* plane = acc + lz * TY * TX;
-          for (int pidx = lane; pidx < W * W; pidx += 32) {
-            const int ay = pidx / W, ax = pidx - ay * W;
-            const int ly = wrap2(sy + ay - T0y, a.g.nf[1]);
-            const int lx = wrap2(sx + ax - T0x, a.g.nf[0]);
-            if (ly < TY && lx < TX) {
-              const T wyx = kk[W + ay] * kk[ax];
-              C* cell = plane + ly * TX + lx;
-              C cur = *cell;
-              cur.x += czr * wyx;
-              cur.y += czi * wyx;
-              *cell = cur;
-            }
-          }
-        }
+  for (int v0 = it.vbeg; v0 < it.vend; v0 += kStageS) {
+    const int cnt = min(kStageS, it.vend - v0);
+    __syncthreads();  // the previous round's readers are done
+    constexpr int NAX = DIM == 3 ? 3 : 2;
+    for (int j = threadIdx.x; j < NAX * cnt; j += blockDim.x) {
+      const int ax = j / cnt, k = j - ax * cnt;
+      const int node = a.vlist[v0 + k];
+      const Pos4<T> pp = pos[node];
+      const ushort4 sl = a.l0[node];
+      if (ax == 0) {
+        es_taps<T, W>(pp.x, beta, px + k * W);
+        oo[k * 4 + 0] = rel_start(sl.x, T0x, nfx, W);
+      } else if (DIM == 3 && ax == 1) {
+        es_taps<T, W>(pp.y, beta, py + k * W);
+        oo[k * 4 + 1] = rel_start(sl.y, T0y, nfy, W);
       } else {
-        // 2D: warp owns local rows ly with ly % kWarps == warp, lanes take the x taps
-        for (int ay = 0; ay < W; ++ay) {
-          const int ly = wrap2(sy + ay - T0y, a.g.nf[1]);
-          if (ly >= TY || (ly % kWarps) != warp) continue;
-          const T wy = kk[W + ay];
-          for (int ax = lane; ax < W; ax += 32) {
-            const int lx = wrap2(sx + ax - T0x, a.g.nf[0]);
-            if (lx < TX) {
-              const T wyx = wy * kk[ax];
-              C* cell = acc + ly * TX + lx;
-              C cur = *cell;
-              cur.x += cq.x * wyx;
-              cur.y += cq.y * wyx;
-              *cell = cur;
-            }
-          }
-        }
+        // the owned axis (z in 3D, y in 2D): store c * psi along it
+        T w[W];
+        es_taps<T, W>(DIM == 3 ? pp.z : pp.y, beta, w);
+        const C cq = cin[node];
+#pragma unroll
+        for (int q = 0; q < W; ++q) cz[k * W + q] = cmk<C>(cq.x * w[q], cq.y * w[q]);
+        const int o = DIM == 3 ? rel_start(sl.z, T0z, nfz, W) : rel_start(sl.y, T0y, nfy, W);
+        oo[k * 4 + 2] = o;
+        if (DIM == 2) oo[k * 4 + 1] = o;
       }
     }
     __syncthreads();
+    for (int p = warp; p < NPL; p += kWarps) {
+      // staged nodes whose taps along the owned axis cover unit p: key in [p - w + 1, p]
+      int lo = 0, hi = cnt;
+      if (!wrp) {
+        int l = 0, h = cnt;
+        while (l < h) { const int m = (l + h) >> 1; if (oo[m * 4 + 2] < p - W + 1) l = m + 1; else h = m; }
+        lo = l;
+        h = cnt;
+        while (l < h) { const int m = (l + h) >> 1; if (oo[m * 4 + 2] <= p) l = m + 1; else h = m; }
+        hi = l;
+      }
+      C* plane = acc + p * PSZ;
+      for (int k = lo; k < hi; ++k) {
+        int az = p - oo[k * 4 + 2];
+        if (wrp) {
+          az = az < 0 ? az + nfp : (az >= nfp ? az - nfp : az);
+          if (az >= W) continue;
+        }
+        const int xx0 = oo[k * 4 + 0] + rx;
+        const int xx = wrx && xx0 < 0 ? xx0 + nfx : xx0;
+        if (rx >= W || xx < 0 || xx >= TX) continue;
+        const C czv = cz[k * W + az];
+        const T wx = px[k * W + rx];
+        if (DIM == 3) {
+          const int oy = oo[k * 4 + 1];
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            const int r = ry + RL * m;
+            const int yy0 = oy + r;
+            const int yy = wry && yy0 < 0 ? yy0 + nfy : yy0;
+            if (r < W && yy >= 0 && yy < TY) {
+              const T w = py[k * W + r] * wx;
+              C* cell = plane + yy * RS + xx;
+              C cur = *cell;
+              cur.x += czv.x * w;
+              cur.y += czv.y * w;
+              *cell = cur;
+            }
+          }
+        } else if (ry == 0) {
+          C* cell = plane + xx;
+          C cur = *cell;
+          cur.x += czv.x * wx;
+          cur.y += czv.y * wx;
+          *cell = cur;
+        }
+      }
+    }
   }
-
-  // write the tile (or this item's partial tile)
+  __syncthreads();
+  const int cells = TX * TY * TZ;
   if (it.slot < 0) {
     C* fine = static_cast<C*>(a.fine);
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
       const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-      const long long off = ((long long)(T0z + lz) * a.g.nf[1] + (T0y + ly)) * a.g.nf[0] + (T0x + lx);
-      fine[off] = acc[i];
+      const long long off = ((long long)(T0z + lz) * nfy + (T0y + ly)) * nfx + (T0x + lx);
+      fine[off] = acc[(lz * TY + ly) * RS + lx];
     }
   } else {
     C* part = static_cast<C*>(a.partial) + (long long)it.slot * cells;
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) part[i] = acc[i];
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+      const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+      part[i] = acc[(lz * TY + ly) * RS + lx];
+    }
   }
 }
 
@@ -375,32 +334,12 @@ __global__ void __launch_bounds__(kThreads) k_spread_atomic(SpreadArgs a, T beta
   C* cv = reinterpret_cast<C*>(acc + 2 * cellsP);               // [kStageA]
   T* kv = reinterpret_cast<T*>(cv + kStageA);                   // [kStageA][3][W]
   int* lv = reinterpret_cast<int*>(kv + kStageA * 3 * W);      // [kStageA][3]
-  __shared__ int nb_begin[8], nb_prefix[9];
 
   const SpreadItem it = a.items[blockIdx.x];
   const int tx = it.tile % a.ntile[0];
   const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
   const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
   const int T0x = tx * TX, T0y = ty * TY, T0z = tz * TZ;
-  if (threadIdx.x == 0) {
-    int k = 0;
-    nb_prefix[0] = 0;
-    for (int dz = 0; dz < (DIM == 3 && a.ntile[2] > 1 ? 2 : 1); ++dz)
-      for (int dy = 0; dy < (a.ntile[1] > 1 ? 2 : 1); ++dy)
-        for (int dx = 0; dx < (a.ntile[0] > 1 ? 2 : 1); ++dx) {
-          const int bx = (tx - dx + a.ntile[0]) % a.ntile[0];
-          const int by = (ty - dy + a.ntile[1]) % a.ntile[1];
-          const int bz = (tz - dz + a.ntile[2]) % a.ntile[2];
-          const int b = (bz * a.ntile[1] + by) * a.ntile[0] + bx;
-          nb_begin[k] = a.bin_start[b];
-          nb_prefix[k + 1] = nb_prefix[k] + (a.bin_start[b + 1] - a.bin_start[b]);
-          ++k;
-        }
-    for (; k < 8; ++k) {
-      nb_begin[k] = 0;
-      nb_prefix[k + 1] = nb_prefix[k];
-    }
-  }
   for (int i = threadIdx.x; i < 2 * cellsP; i += blockDim.x) acc[i] = (T)0;
   __syncthreads();
 
@@ -416,10 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_atomic(SpreadArgs a, T beta
     for (int j = threadIdx.x; j < 3 * cnt; j += blockDim.x) {
       const int ax = j / cnt, k = j - ax * cnt;
       if (DIM == 2 && ax == 2) continue;
-      const int v = v0 + k;
-      int b = 0;
-      while (v >= nb_prefix[b + 1]) ++b;
-      const int node = nb_begin[b] + (v - nb_prefix[b]);
+      const int node = a.vlist[v0 + k];
       const Pos4<T> pp = pos[node];
       es_taps<T, W>(ax == 0 ? pp.x : (ax == 1 ? pp.y : pp.z), beta, kv + (k * 3 + ax) * W);
       if (ax == 0) {
@@ -538,6 +474,9 @@ __global__ void __launch_bounds__(kThreads) k_spread_atomic(SpreadArgs a, T beta
   }
 }
 
+// Sums the partial tiles of split tiles; blockIdx.y selects a slice of the tile's cells
+// so that the few, large split tiles still spread over the whole GPU.
+constexpr int kReduceSlices = 8;
 template <typename T>
 __global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __restrict__ partial,
                          cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx,
@@ -545,8 +484,10 @@ __global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __r
   using C = cx_t<T>;
   const SplitTile st = split[blockIdx.x];
   const int cells = TX * TY * TZ;
+  const int per = (cells + kReduceSlices - 1) / kReduceSlices;
+  const int c0 = blockIdx.y * per, c1 = min(cells, c0 + per);
   const int tx = st.tile % ntx, ty = (st.tile / ntx) % nty, tz = st.tile / (ntx * nty);
-  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+  for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     T sr = 0, si = 0;
     for (int k = 0; k < st.nslots; ++k) {
       const C v = partial[(long long)(st.slot0 + k) * cells + i];
@@ -560,7 +501,6 @@ __global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __r
   }
 }
 
-// ---- launch helpers ----------------------------------------------------------------------------
 GridDims dims_of(const Plan& p) {
   GridDims g;
   for (int d = 0; d < 3; ++d) {
@@ -570,12 +510,6 @@ GridDims dims_of(const Plan& p) {
   return g;
 }
 
-unsigned grid_for(long long work, int threads) {
-  long long b = (work + threads - 1) / threads;
-  if (b > 152LL * 32) b = 152LL * 32;
-  if (b < 1) b = 1;
-  return (unsigned)b;
-}
 
 template <typename T, int W, int DIM>
 int launch_interp(const Plan& p, cudaStream_t s) {
@@ -588,12 +522,14 @@ int launch_interp(const Plan& p, cudaStream_t s) {
 }
 
 size_t spread_smem(const Plan& p) {
-  const size_t cells = (size_t)p.tile[0] * p.tile[1] * p.tile[2];
-  const size_t rs = p.real_size();
-  if (p.spread_method == 1)
-    return cells * p.cx_size() + kStage * p.cx_size() + (size_t)kStage * 3 * p.w * rs + kStage * 3 * sizeof(int);
-  const size_t cellsP = (size_t)p.tile[2] * atomic_plane_stride(p.tile[0], p.tile[1]);
-  return cellsP * p.cx_size() + kStageA * p.cx_size() + (size_t)kStageA * 3 * p.w * rs + kStageA * 3 * sizeof(int);
+  const size_t rs = p.real_size(), cs = p.cx_size();
+  if (p.spread_method == 2) {
+    const size_t cellsP = (size_t)p.tile[2] * atomic_plane_stride(p.tile[0], p.tile[1]);
+    return cellsP * cs + kStageA * cs + (size_t)kStageA * 3 * p.w * rs + kStageA * 3 * sizeof(int);
+  }
+  const size_t rsx = spread_row_stride(p.tile[0]);
+  const size_t cells = p.dim == 3 ? (size_t)p.tile[2] * p.tile[1] * rsx : (size_t)p.tile[1] * rsx;
+  return cells * cs + (size_t)kStageS * p.w * cs + 2 * (size_t)kStageS * p.w * rs + kStageS * 4 * sizeof(int);
 }
 
 template <typename T, int W, int DIM>
@@ -605,15 +541,16 @@ int launch_spread(const Plan& p, cudaStream_t s) {
     a.ntile[d] = p.ntile[d];
   }
   a.items = p.d_items;
-  a.bin_start = p.d_bin_start;
+  a.vlist = p.d_vlist;
   a.l0 = static_cast<const ushort4*>(p.d_l0);
   a.pos = p.d_pos;
   a.c = p.d_c;
   a.fine = p.d_fine;
   a.partial = p.d_partial;
   const size_t smem = spread_smem(p);
-  auto kern = p.spread_method == 1 ? k_spread<T, W, DIM>
-                                   : (W <= 8 ? k_spread_atomic<T, W, DIM, true> : k_spread_atomic<T, W, DIM, false>);
+  auto kern = p.spread_method == 2
+                  ? (W <= 8 ? k_spread_atomic<T, W, DIM, true> : k_spread_atomic<T, W, DIM, false>)
+                  : k_spread_planes<T, W, DIM>;
   if (smem > 48 * 1024) {
     DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
@@ -621,7 +558,7 @@ int launch_spread(const Plan& p, cudaStream_t s) {
   DDI_LAUNCH_CHECK();
   const_cast<Plan&>(p).mark("spread", s);
   if (p.nsplit > 0) {
-    k_reduce<T><<<p.nsplit, kThreads, 0, s>>>(p.d_split, static_cast<const cx_t<T>*>(p.d_partial),
+    k_reduce<T><<<dim3(p.nsplit, kReduceSlices), kThreads, 0, s>>>(p.d_split, static_cast<const cx_t<T>*>(p.d_partial),
                                               static_cast<cx_t<T>*>(p.d_fine), dims_of(p), p.tile[0],
                                               p.tile[1], p.tile[2], p.ntile[0], p.ntile[1]);
     DDI_LAUNCH_CHECK();
@@ -672,17 +609,7 @@ int spread_w(const Plan& p, cudaStream_t s) {
 
 template <typename T>
 int run_type2(Plan& p, const T* rho, cudaStream_t s) {
-  using C = cx_t<T>;
-  C* fine = static_cast<C*>(p.d_fine);
-  k_pad<T><<<grid_for(p.fine_points(), kThreads), kThreads, 0, s>>>(rho, fine, static_cast<const T*>(p.d_deconv),
-                                                                     dims_of(p));
-  DDI_LAUNCH_CHECK();
-  p.mark("pad", s);
-  static const char* names[3] = {"fft_x_fwd", "fft_y_fwd", "fft_z_fwd"};
-  for (int a = 0; a < p.dim; ++a) {
-    DDI_TRY(fft_axis<T>(p, fine, p.nf[0], p.nf[1], p.nf[2], a, -1, s));
-    p.mark(names[a], s);
-  }
+  DDI_TRY(nufft_forward_fft<T>(p, rho, s));
   DDI_TRY((p.dim == 3 ? interp_w<T, 3>(p, s) : interp_w<T, 2>(p, s)));
   p.mark("interp", s);
   return DDI_OK;
@@ -690,19 +617,8 @@ int run_type2(Plan& p, const T* rho, cudaStream_t s) {
 
 template <typename T>
 int run_type1(Plan& p, T* phi, cudaStream_t s) {
-  using C = cx_t<T>;
-  C* fine = static_cast<C*>(p.d_fine);
   DDI_TRY(p.dim == 3 ? (spread_w<T, 3>(p, s)) : (spread_w<T, 2>(p, s)));
-  static const char* names[3] = {"fft_x_inv", "fft_y_inv", "fft_z_inv"};
-  for (int a = 0; a < p.dim; ++a) {
-    DDI_TRY(fft_axis<T>(p, fine, p.nf[0], p.nf[1], p.nf[2], a, +1, s));
-    p.mark(names[a], s);
-  }
-  k_crop<T><<<grid_for(p.grid_points(), kThreads), kThreads, 0, s>>>(fine, phi, static_cast<const T*>(p.d_deconv),
-                                                                     dims_of(p));
-  DDI_LAUNCH_CHECK();
-  p.mark("crop", s);
-  return DDI_OK;
+  return nufft_inverse_fft<T>(p, phi, s);
 }
 
 template <typename T>
@@ -746,7 +662,7 @@ int dev_alloc(Plan& p, void** ptr, size_t bytes, const char* what) {
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_l0, p.d_pos, p.d_c, p.d_deconv, p.d_fine, p.d_partial, p.d_bin_start, p.d_items,
+  void* ptrs[] = {p.d_l0, p.d_pos, p.d_c, p.d_deconv, p.d_fine, p.d_partial, p.d_bin_start, p.d_vlist, p.d_items,
                   p.d_split, p.d_psi1, p.d_rho, p.d_phi, p.d_work, p.d_work2, p.d_kin, p.d_red, p.d_io_in, p.d_io_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -774,15 +690,13 @@ void choose_tile(Plan& p) {
   const int need = p.w - 1;
   int want[3];
   if (p.dim == 3) {
-    if (p.spread_method == 1) {
-      want[0] = 16; want[1] = 16; want[2] = p.prec == DDI_FP32 ? 8 : 16;
-    } else if (p.prec == DDI_FP32) {
-      want[0] = 32; want[1] = 16; want[2] = 16;
+    if (p.prec == DDI_FP32) {
+      want[0] = 32; want[1] = 32; want[2] = 8;
     } else {
       want[0] = 16; want[1] = 16; want[2] = 16;
     }
   } else {
-    want[0] = 64; want[1] = 32; want[2] = 1;
+    want[0] = 64; want[1] = 64; want[2] = 1;
   }
   for (int d = 0; d < 3; ++d) {
     if (p.desc.tile[d] > 0) want[d] = p.desc.tile[d];
@@ -814,7 +728,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   }
   p.w = kernel_width(d);
   p.beta = kernel_beta(p.w);
-  p.spread_method = d.spread_method == 1 ? 1 : 2;
+  p.spread_method = d.spread_method == 2 ? 2 : 1;
   build_quadrature(d, &p.quad);
   p.M = p.quad.M;
   choose_tile(p);
@@ -870,41 +784,64 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
     scs[i] = sc[o];
   }
 
-  // spread work list: per tile, its visit count (own bin + lower neighbours), split in chunks
-  std::vector<int> visits(p.nbins, 0);
-  long long total = 0;
-  for (int tz = 0; tz < p.ntile[2]; ++tz)
-    for (int ty = 0; ty < p.ntile[1]; ++ty)
-      for (int tx = 0; tx < p.ntile[0]; ++tx) {
-        int v = 0;
-        for (int dz = 0; dz < (dim == 3 && p.ntile[2] > 1 ? 2 : 1); ++dz)
-          for (int dy = 0; dy < (p.ntile[1] > 1 ? 2 : 1); ++dy)
-            for (int dx = 0; dx < (p.ntile[0] > 1 ? 2 : 1); ++dx) {
-              const int bx = (tx - dx + p.ntile[0]) % p.ntile[0];
-              const int by = (ty - dy + p.ntile[1]) % p.ntile[1];
-              const int bz = (tz - dz + p.ntile[2]) % p.ntile[2];
-              const int b = (bz * p.ntile[1] + by) * p.ntile[0] + bx;
-              v += bin_start[b + 1] - bin_start[b];
-            }
-        visits[(tz * p.ntile[1] + ty) * p.ntile[0] + tx] = v;
-        total += v;
+  // spread work list: per tile, the nodes whose taps reach it, sorted by their start
+  // relative to the tile (oz, oy, ox); long lists are cut into items writing partial tiles
+  std::vector<std::vector<std::pair<int64_t, int>>> lists(p.nbins);
+  {
+    for (int64_t i = 0; i < p.Mh; ++i) {
+      int ta[3][2], nt[3];
+      const int lv[3] = {l0s[i].x, l0s[i].y, l0s[i].z};
+      for (int a = 0; a < 3; ++a) {
+        const int l = a < dim ? lv[a] : 0;
+        const int w = a < dim ? p.w : 1;
+        const int t0 = l / p.tile[a];
+        const int t1 = ((l + w - 1) % p.nf[a]) / p.tile[a];
+        ta[a][0] = t0;
+        ta[a][1] = t1;
+        nt[a] = t1 != t0 ? 2 : 1;
       }
-  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(1024, total / (152LL * 8));
+      for (int cz = 0; cz < nt[2]; ++cz)
+        for (int cy = 0; cy < nt[1]; ++cy)
+          for (int cx = 0; cx < nt[0]; ++cx) {
+            const int bx = ta[0][cx], by = ta[1][cy], bz = ta[2][cz];
+            const int t = (bz * p.ntile[1] + by) * p.ntile[0] + bx;
+            const int ox = rel_start(l0s[i].x, bx * p.tile[0], p.nf[0], p.w);
+            const int oy = dim >= 2 ? rel_start(l0s[i].y, by * p.tile[1], p.nf[1], p.w) : 0;
+            const int oz = dim == 3 ? rel_start(l0s[i].z, bz * p.tile[2], p.nf[2], p.w) : 0;
+            // major key: the owned axis (z in 3D, y in 2D); starts lie in [-15, 2048)
+            const int64_t key = dim == 3 ? (((int64_t)oz + 32) * 4096 + (oy + 32)) * 4096 + (ox + 32)
+                                         : ((int64_t)oy + 32) * 4096 + (ox + 32);
+            lists[t].push_back(std::make_pair(key, (int)i));
+          }
+    }
+  }
+  long long total = 0;
+  for (auto& L : lists) {
+    std::stable_sort(L.begin(), L.end(),
+                     [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) { return a.first < b.first; });
+    total += (long long)L.size();
+  }
+  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(512, total / (152LL * 6));
+  std::vector<int> vlist;
+  vlist.reserve(total);
   std::vector<SpreadItem> items;
   std::vector<SplitTile> split;
   int slot = 0;
   for (int t = 0; t < p.nbins; ++t) {
-    const int v = visits[t];
+    const int beg = (int)vlist.size();
+    for (auto& e : lists[t]) vlist.push_back(e.second);
+    const int v = (int)lists[t].size();
     if (v <= p.chunk) {
-      items.push_back(SpreadItem{t, 0, v, -1});
+      items.push_back(SpreadItem{t, beg, beg + v, -1});
     } else {
       const int nch = (v + p.chunk - 1) / p.chunk;
       split.push_back(SplitTile{t, slot, nch, 0});
       for (int c = 0; c < nch; ++c)
-        items.push_back(SpreadItem{t, c * p.chunk, std::min(v, (c + 1) * p.chunk), slot + c});
+        items.push_back(SpreadItem{t, beg + c * p.chunk, beg + std::min(v, (c + 1) * p.chunk), slot + c});
       slot += nch;
     }
   }
+  p.visits = total;
   // heaviest items first so the long ones start early
   std::stable_sort(items.begin(), items.end(),
                    [](const SpreadItem& a, const SpreadItem& b) { return (a.vend - a.vbeg) > (b.vend - b.vbeg); });
@@ -935,6 +872,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
   DDI_TRY(dev_alloc(p, &p.d_partial, cs * cells * std::max(1, p.nslots), "partial tiles"));
   DDI_TRY(dev_alloc(p, (void**)&p.d_bin_start, sizeof(int) * bin_start.size(), "bins"));
+  DDI_TRY(dev_alloc(p, (void**)&p.d_vlist, sizeof(int) * std::max<size_t>(1, vlist.size()), "visit lists"));
   DDI_TRY(dev_alloc(p, (void**)&p.d_items, sizeof(SpreadItem) * items.size(), "work items"));
   DDI_TRY(dev_alloc(p, (void**)&p.d_split, sizeof(SplitTile) * std::max<size_t>(1, split.size()), "split tiles"));
   const size_t N = (size_t)p.grid_points();
@@ -969,6 +907,8 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   DDI_CUDA(cudaMemcpyAsync(p.d_deconv, dcb.data(), dcb.size(), cudaMemcpyHostToDevice, stream));
   DDI_CUDA(cudaMemcpyAsync(p.d_bin_start, bin_start.data(), sizeof(int) * bin_start.size(), cudaMemcpyHostToDevice,
                            stream));
+  if (!vlist.empty())
+    DDI_CUDA(cudaMemcpyAsync(p.d_vlist, vlist.data(), sizeof(int) * vlist.size(), cudaMemcpyHostToDevice, stream));
   DDI_CUDA(cudaMemcpyAsync(p.d_items, items.data(), sizeof(SpreadItem) * items.size(), cudaMemcpyHostToDevice,
                            stream));
   if (!split.empty())

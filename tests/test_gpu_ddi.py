@@ -77,11 +77,11 @@ def test_ddi_mixture_tilted_48(D, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_ddi_plane_owned_spread_variant(D, precision):
-    # the alternative spread (warps own z-planes, no atomics) gives the same result
+def test_ddi_atomic_spread_variant(D, precision):
+    # the alternative spread (shared-memory atomics, nodes split between warps)
     w = synth.gaussian_mixture_density(48, 8.0, seed=4)
     plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=48, ntheta=24, nphi=48,
-                 spread_method=1)
+                 spread_method=2)
     got = _run(D, plan, w["rho"])
     ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(48, 24, 48))
     assert _relinf(got, ref) <= TOL[precision]

@@ -54,7 +54,9 @@ constexpr int kWarps = kThreads / 32;
 
 template <typename T> struct Pos4 { T x, y, z, w; };
 
-__device__ __forceinline__ float es_exp(float v) { return expf(v); }
+// FP32: the hardware exponential (relative error a few ulp near the kernel centre, where
+// psi is O(1); larger only where psi < 1e-6) with an IEEE square root
+__device__ __forceinline__ float es_exp(float v) { return __expf(v); }
 __device__ __forceinline__ double es_exp(double v) { return exp(v); }
 __device__ __forceinline__ float es_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double es_sqrt(double v) { return sqrt(v); }
@@ -161,11 +163,25 @@ __host__ __device__ inline int rel_start(int l0, int T0, int nf, int w) {
   if (o > nf - w) o -= nf;
   return o;
 }
-// padded row stride (cells) of the plane-owned accumulator: = 8 (mod 16) so that the two
-// 8-cell row segments one half-warp touches fall in different halves of the banks
-__host__ __device__ inline int spread_row_stride(int TX) { return TX + ((8 - TX % 16) + 16) % 16; }
+// Row stride (cells) of the plane-owned accumulator.  A half-warp touches two 8-cell row
+// segments; they must fall in different halves of the 128-byte bank window.  Rows of a
+// multiple of 16 cells are unpadded and swizzled (x ^ 8 on odd rows); other widths are
+// padded to a stride = 8 (mod 16).
+__host__ __device__ inline bool spread_swizzle(int TX) { return TX % 16 == 0; }
+// first fine cell of tile t along an axis: t T - T/2 (mod nf); unshifted with one tile
+__host__ __device__ inline int tile_origin(int t, int T, int ntile, int nf) {
+  if (ntile == 1) return 0;
+  int o = t * T - T / 2;
+  return o < 0 ? o + nf : o;
+}
+__host__ __device__ inline int spread_row_stride(int TX) {
+  return spread_swizzle(TX) ? TX : TX + ((8 - TX % 16) + 16) % 16;
+}
+__device__ __forceinline__ int spread_cell(int y, int x, int RS, bool swz) {
+  return y * RS + (swz ? (x ^ ((y & 1) << 3)) : x);
+}
 
-constexpr int kStageS = 128;  // nodes staged per round in k_spread_planes
+constexpr int kStageS = 64;  // nodes staged per round in k_spread_planes
 
 // Plane-owned spread (no atomics).  A CTA owns a fine-grid tile; its visit list holds
 // exactly the nodes whose w^d taps reach the tile, sorted by relative start
@@ -184,20 +200,25 @@ __global__ void __launch_bounds__(kThreads) k_spread_planes(SpreadArgs a, T beta
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
   const int RS = spread_row_stride(TX);
+  const bool swz = spread_swizzle(TX);
   const int NPL = DIM == 3 ? TZ : TY;          // owned units: z-planes (3D) or y-rows (2D)
   const int PSZ = DIM == 3 ? TY * RS : RS;     // cells per owned unit
   C* acc = reinterpret_cast<C*>(smem_raw);     // [NPL][PSZ]
   C* cz = acc + NPL * PSZ;                     // [kStageS][W]: c psi_z (3D) / c psi_y (2D)
   T* py = reinterpret_cast<T*>(cz + kStageS * W);  // [kStageS][W] (3D only)
   T* px = py + kStageS * W;                    // [kStageS][W]
-  int* oo = reinterpret_cast<int*>(px + kStageS * W);  // [kStageS][4]: ox, oy, oz, plane key
+  int* oo = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(px + kStageS * W) + 15) &
+                                   ~static_cast<uintptr_t>(15));  // [kStageS][4]: ox, oy, oz, -
 
   const SpreadItem it = a.items[blockIdx.x];
   const int tx = it.tile % a.ntile[0];
   const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
   const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
-  const int T0x = tx * TX, T0y = ty * TY, T0z = tz * TZ;
   const int nfx = a.g.nf[0], nfy = a.g.nf[1], nfz = a.g.nf[2];
+  // the tile lattice is shifted by half a tile so that k = 0 sits inside a tile
+  const int T0x = tile_origin(tx, TX, a.ntile[0], nfx);
+  const int T0y = tile_origin(ty, TY, a.ntile[1], nfy);
+  const int T0z = tile_origin(tz, TZ, a.ntile[2], nfz);
   const bool wrx = a.ntile[0] == 1, wry = a.ntile[1] == 1, wrz = a.ntile[2] == 1;
   const bool wrp = DIM == 3 ? wrz : wry;       // owned axis wraps inside the tile
   const int nfp = DIM == 3 ? nfz : nfy;
@@ -249,6 +270,52 @@ __global__ void __launch_bounds__(kThreads) k_spread_planes(SpreadArgs a, T beta
         hi = l;
       }
       C* plane = acc + p * PSZ;
+      if (!(wrx || wry || wrp)) {
+        // fast path: no periodic wrap inside the tile.  Consecutive nodes with the same
+        // (oy, ox) hit the same cells of this plane: they are summed in registers and the
+        // plane is updated once per run.
+        T ar[MR], ai[MR];
+#pragma unroll
+        for (int m = 0; m < MR; ++m) ar[m] = ai[m] = (T)0;
+        int run_x = INT_MIN, run_y = 0;
+        for (int k = lo; k <= hi; ++k) {
+          int4 o = make_int4(INT_MIN, 0, 0, 0);
+          if (k < hi) o = *reinterpret_cast<const int4*>(oo + k * 4);
+          if (o.x != run_x || o.y != run_y) {
+            if (run_x != INT_MIN) {
+              const int xx = run_x + rx;
+              if (rx < W && (unsigned)xx < (unsigned)TX) {
+#pragma unroll
+                for (int m = 0; m < (DIM == 3 ? MR : 1); ++m) {
+                  const int r = DIM == 3 ? ry + RL * m : 0;
+                  const int yy = run_y + r;
+                  if ((DIM == 3 && (r >= W || (unsigned)yy >= (unsigned)TY)) || (DIM == 2 && ry != 0)) continue;
+                  C* cell = plane + (DIM == 3 ? spread_cell(yy, xx, RS, swz) : xx);
+                  C cur = *cell;
+                  cur.x += ar[m];
+                  cur.y += ai[m];
+                  *cell = cur;
+                }
+              }
+#pragma unroll
+              for (int m = 0; m < MR; ++m) ar[m] = ai[m] = (T)0;
+            }
+            run_x = o.x;
+            run_y = o.y;
+          }
+          if (k == hi) break;
+          const C czv = cz[k * W + (p - o.z)];
+          const T wx = rx < W ? px[k * W + rx] : (T)0;
+#pragma unroll
+          for (int m = 0; m < (DIM == 3 ? MR : 1); ++m) {
+            const int r = DIM == 3 ? ry + RL * m : 0;
+            const T w = DIM == 3 ? (r < W ? py[k * W + r] : (T)0) * wx : wx;
+            ar[m] += czv.x * w;
+            ai[m] += czv.y * w;
+          }
+        }
+        continue;
+      }
       for (int k = lo; k < hi; ++k) {
         int az = p - oo[k * 4 + 2];
         if (wrp) {
@@ -269,7 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_planes(SpreadArgs a, T beta
             const int yy = wry && yy0 < 0 ? yy0 + nfy : yy0;
             if (r < W && yy >= 0 && yy < TY) {
               const T w = py[k * W + r] * wx;
-              C* cell = plane + yy * RS + xx;
+              C* cell = plane + spread_cell(yy, xx, RS, swz);
               C cur = *cell;
               cur.x += czv.x * w;
               cur.y += czv.y * w;
@@ -292,14 +359,16 @@ __global__ void __launch_bounds__(kThreads) k_spread_planes(SpreadArgs a, T beta
     C* fine = static_cast<C*>(a.fine);
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
       const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-      const long long off = ((long long)(T0z + lz) * nfy + (T0y + ly)) * nfx + (T0x + lx);
-      fine[off] = acc[(lz * TY + ly) * RS + lx];
+      const int gx = T0x + lx, gy = T0y + ly, gz = T0z + lz;
+      const long long off = ((long long)(gz >= nfz ? gz - nfz : gz) * nfy + (gy >= nfy ? gy - nfy : gy)) * nfx +
+                            (gx >= nfx ? gx - nfx : gx);
+      fine[off] = acc[DIM == 3 ? lz * PSZ + spread_cell(ly, lx, RS, swz) : ly * PSZ + lx];
     }
   } else {
     C* part = static_cast<C*>(a.partial) + (long long)it.slot * cells;
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
       const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-      part[i] = acc[(lz * TY + ly) * RS + lx];
+      part[i] = acc[DIM == 3 ? lz * PSZ + spread_cell(ly, lx, RS, swz) : ly * PSZ + lx];
     }
   }
 }
@@ -339,7 +408,9 @@ __global__ void __launch_bounds__(kThreads) k_spread_atomic(SpreadArgs a, T beta
   const int tx = it.tile % a.ntile[0];
   const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
   const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
-  const int T0x = tx * TX, T0y = ty * TY, T0z = tz * TZ;
+  const int T0x = tile_origin(tx, TX, a.ntile[0], a.g.nf[0]);
+  const int T0y = tile_origin(ty, TY, a.ntile[1], a.g.nf[1]);
+  const int T0z = tile_origin(tz, TZ, a.ntile[2], a.g.nf[2]);
   for (int i = threadIdx.x; i < 2 * cellsP; i += blockDim.x) acc[i] = (T)0;
   __syncthreads();
 
@@ -460,7 +531,9 @@ __global__ void __launch_bounds__(kThreads) k_spread_atomic(SpreadArgs a, T beta
     C* fine = static_cast<C*>(a.fine);
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
       const int lx = i % TX, ly2 = (i / TX) % TY, lz2 = i / (TX * TY);
-      const long long off = ((long long)(T0z + lz2) * nfy + (T0y + ly2)) * nfx + (T0x + lx);
+      const int gx = T0x + lx, gy = T0y + ly2, gz = T0z + lz2;
+      const long long off = ((long long)(gz >= nfz ? gz - nfz : gz) * nfy + (gy >= nfy ? gy - nfy : gy)) * nfx +
+                            (gx >= nfx ? gx - nfx : gx);
       const int pi = lz2 * PS + ly2 * RS + lx;
       fine[off] = cmk<C>(acc[pi], acc[cellsP + pi]);
     }
@@ -495,8 +568,13 @@ __global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __r
       si += v.y;
     }
     const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-    const long long off =
-        ((long long)(tz * TZ + lz) * g.nf[1] + (ty * TY + ly)) * g.nf[0] + (tx * TX + lx);
+    int gx = tile_origin(tx, TX, ntx, g.nf[0]) + lx;
+    int gy = tile_origin(ty, TY, nty, g.nf[1]) + ly;
+    int gz = tile_origin(tz, TZ, g.nf[2] / TZ, g.nf[2]) + lz;
+    gx -= gx >= g.nf[0] ? g.nf[0] : 0;
+    gy -= gy >= g.nf[1] ? g.nf[1] : 0;
+    gz -= gz >= g.nf[2] ? g.nf[2] : 0;
+    const long long off = ((long long)gz * g.nf[1] + gy) * g.nf[0] + gx;
     fine[off] = cmk<C>(sr, si);
   }
 }
@@ -529,7 +607,7 @@ size_t spread_smem(const Plan& p) {
   }
   const size_t rsx = spread_row_stride(p.tile[0]);
   const size_t cells = p.dim == 3 ? (size_t)p.tile[2] * p.tile[1] * rsx : (size_t)p.tile[1] * rsx;
-  return cells * cs + (size_t)kStageS * p.w * cs + 2 * (size_t)kStageS * p.w * rs + kStageS * 4 * sizeof(int);
+  return cells * cs + (size_t)kStageS * p.w * cs + 2 * (size_t)kStageS * p.w * rs + kStageS * 4 * sizeof(int) + 16;
 }
 
 template <typename T, int W, int DIM>
@@ -794,8 +872,9 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
       for (int a = 0; a < 3; ++a) {
         const int l = a < dim ? lv[a] : 0;
         const int w = a < dim ? p.w : 1;
-        const int t0 = l / p.tile[a];
-        const int t1 = ((l + w - 1) % p.nf[a]) / p.tile[a];
+        const int sh = p.ntile[a] > 1 ? p.tile[a] / 2 : 0;  // lattice shift (tile_origin)
+        const int t0 = ((l + sh) % p.nf[a]) / p.tile[a];
+        const int t1 = ((l + w - 1 + sh) % p.nf[a]) / p.tile[a];
         ta[a][0] = t0;
         ta[a][1] = t1;
         nt[a] = t1 != t0 ? 2 : 1;
@@ -805,9 +884,10 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
           for (int cx = 0; cx < nt[0]; ++cx) {
             const int bx = ta[0][cx], by = ta[1][cy], bz = ta[2][cz];
             const int t = (bz * p.ntile[1] + by) * p.ntile[0] + bx;
-            const int ox = rel_start(l0s[i].x, bx * p.tile[0], p.nf[0], p.w);
-            const int oy = dim >= 2 ? rel_start(l0s[i].y, by * p.tile[1], p.nf[1], p.w) : 0;
-            const int oz = dim == 3 ? rel_start(l0s[i].z, bz * p.tile[2], p.nf[2], p.w) : 0;
+            const int ox = rel_start(l0s[i].x, tile_origin(bx, p.tile[0], p.ntile[0], p.nf[0]), p.nf[0], p.w);
+            const int oy = rel_start(l0s[i].y, tile_origin(by, p.tile[1], p.ntile[1], p.nf[1]), p.nf[1], p.w);
+            const int oz = dim == 3 ? rel_start(l0s[i].z, tile_origin(bz, p.tile[2], p.ntile[2], p.nf[2]), p.nf[2], p.w)
+                                    : 0;
             // major key: the owned axis (z in 3D, y in 2D); starts lie in [-15, 2048)
             const int64_t key = dim == 3 ? (((int64_t)oz + 32) * 4096 + (oy + 32)) * 4096 + (ox + 32)
                                          : ((int64_t)oy + 32) * 4096 + (ox + 32);

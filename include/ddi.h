@@ -63,9 +63,9 @@ typedef struct {
   double kmax;         /* radius R of the Fourier ball; 0 => pi / min_d h_d */
   int precision;       /* DDI_FP64 or DDI_FP32 */
   double nufft_tol;    /* requested NUFFT tolerance; 0 => 1e-13 (FP64) / 1e-6 (FP32) */
-  int tile[3];         /* spread tile (x, y, z) in fine cells; 0 => built-in choice */
+  int tile[3];         /* spread tile (x, y, z) in fine cells, >= w - 1 and dividing 2n (rounded to
+                          such a size); 0 => built-in choice */
   int chunk;           /* max nodes per spread work item; 0 => built-in choice */
-  int spread_method;   /* 0 => default (1); 1 => warps own tile planes; 2 => shared-memory atomics */
 } ddi_plan_desc;
 
 /* Read-only facts about a built plan (sizes and the NUFFT parameters chosen). */

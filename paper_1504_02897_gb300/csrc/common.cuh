@@ -74,6 +74,36 @@ struct SplitTile {
   int tile, slot0, nslots, pad;
 };
 
+// ---- spread tile geometry (host and device) -------------------------------------------------
+constexpr int kSpreadThreads = 512;  // at most one warp per owned plane, 16 warps
+
+// first fine cell of tile t along an axis: t T - T/2 (mod nf), i.e. the tile lattice is
+// shifted by half a tile so that k = 0 lies inside a tile; unshifted with a single tile
+__host__ __device__ inline int tile_origin(int t, int T, int ntile, int nf) {
+  if (ntile == 1) return 0;
+  const int o = t * T - T / 2;
+  return o < 0 ? o + nf : o;
+}
+// start of a footprint relative to a tile origin: l0 - T0 wrapped into [-(w-1), nf-(w-1)),
+// so that footprints reaching the tile from below through the periodic wrap are negative
+__host__ __device__ inline int rel_start(int l0, int T0, int nf, int w) {
+  int o = l0 - T0;
+  if (o < 0) o += nf;
+  if (o > nf - w) o -= nf;
+  return o;
+}
+// Row stride (cells) of the spread's shared-memory tile.  A half-warp touches two 8-cell
+// row segments; they must fall in different halves of the 128-byte bank window.  Rows of
+// a multiple of 16 cells are unpadded and swizzled (x ^ 8 on odd rows); other widths are
+// padded to a stride = 8 (mod 16).
+__host__ __device__ inline bool spread_swizzle(int TX) { return TX % 16 == 0; }
+__host__ __device__ inline int spread_row_stride(int TX) {
+  return spread_swizzle(TX) ? TX : TX + ((8 - TX % 16) + 16) % 16;
+}
+__host__ __device__ inline int spread_cell(int y, int x, int RS, bool swz) {
+  return y * RS + (swz ? (x ^ ((y & 1) << 3)) : x);
+}
+
 // ---- the plan ----------------------------------------------------------------------
 struct Plan {
   ddi_plan_desc desc{};
@@ -87,27 +117,29 @@ struct Plan {
   int64_t M = 0, Mh = 0;
   int tile[3] = {1, 1, 1};
   int ntile[3] = {1, 1, 1};
-  int nbins = 0;
   int chunk = 0;
-  int spread_method = 1;  // 1: warps own z-planes (no atomics), 2: shared-memory atomics
   int device = 0;
   size_t bytes = 0;
 
   QuadTables quad;                   // host copy of the tables (export, tests)
   std::vector<int64_t> order;        // processing order -> original node index
 
-  // device arrays (element types depend on prec)
+  // device arrays (element types depend on prec), nodes in processing order
   void* d_l0 = nullptr;       // ushort4 [Mh]: wrapped first tap (x, y, z)
-  void* d_pos = nullptr;      // T4 [Mh]: (fx, fy, fz, 2 h^d W_q), f = s - l0 - w/2
-  void* d_c = nullptr;        // cx [Mh]: node values between interp and spread
+  void* d_psi = nullptr;      // T [Mh][3][w]: kernel values along x, y, z at the w taps
+  void* d_scale = nullptr;    // T [Mh]: 2 h^d W_q
+  void* d_c = nullptr;        // cx [Mh]: node values c_q
+  void* d_cz = nullptr;       // cx [Mh][w]: c_q times the kernel along the spread's owned axis
   void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
   void* d_partial = nullptr;  // cx [nslots * tile cells]
-  int* d_bin_start = nullptr; // [nbins + 1]
-  int* d_vlist = nullptr;     // spread visit lists (node indices), per tile
-  long long visits = 0;       // total list entries
+  int4* d_visits = nullptr;   // spread visit lists: (node, ox, oy, oz) relative to the tile
+  int2* d_prng = nullptr;     // [item][npl] visit range of each owned plane
   SpreadItem* d_items = nullptr;
   SplitTile* d_split = nullptr;
+  long long visits = 0;       // total visit-list entries
+  int npl = 1;                // owned units per tile (z-planes in 3D, y-rows in 2D)
+  int spread_threads = 256;
   int nitems = 0, nsplit = 0, nslots = 0;
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n}
@@ -138,6 +170,10 @@ struct Plan {
   }
 
   int64_t grid_points() const { return (int64_t)n[0] * n[1] * n[2]; }
+  size_t spread_tile_cells() const {
+    const size_t rs = (size_t)spread_row_stride(tile[0]);
+    return dim == 3 ? (size_t)tile[2] * tile[1] * rs : (size_t)tile[1] * rs;
+  }
   int64_t fine_points() const { return (int64_t)nf[0] * nf[1] * nf[2]; }
   size_t real_size() const { return prec == DDI_FP64 ? 8 : 4; }
   size_t cx_size() const { return prec == DDI_FP64 ? 16 : 8; }
@@ -163,9 +199,14 @@ template <typename T> int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t 
 template <typename T> int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s);        // U (fine grid) -> phi
 
 // ---- NUFFT stages (nufft.cu) --------------------------------------------------------
-template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);       // rho -> d_c
-template <typename T> int run_type1(Plan& p, T* phi, cudaStream_t s);             // d_c -> phi
+template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);         // rho -> d_c, d_cz
+template <typename T> int run_type1_from_c(Plan& p, T* phi, cudaStream_t s);       // d_c -> phi
 template <typename T> int run_ddi(Plan& p, const T* rho, T* phi, cudaStream_t s);
+inline size_t spread_smem_bytes(const Plan& p) { return p.spread_tile_cells() * p.cx_size(); }
+
+// ---- plans (plan.cu) ------------------------------------------------------------------------
+int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream);
+void destroy_plan(Plan& p);
 
 }  // namespace ddi
 

@@ -1,0 +1,540 @@
+// Plan construction and the DDI entry points of the C ABI.
+//
+// A plan holds everything that depends only on the grid, the box, the dipole axes and
+// the quadrature (Sec. 2.1, Eq. DDI-Trun1): the node tables (tables.cpp), for each node
+// of one half of the antipodally closed set its first fine-grid tap, its kernel values
+// psi_d at the w taps of each axis (FP64, rounded once) and its scale 2 h^d W_q, the
+// deconvolution factors, the spread work list (per fine-grid tile, the nodes whose taps
+// reach it, in order of their start relative to the tile, cut into work items), and all
+// device workspace.  ddi_plan_create is the only call that allocates.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "common.cuh"
+
+namespace ddi {
+
+// ---- error reporting -----------------------------------------------------------------
+namespace {
+thread_local std::string g_err;
+}
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+const char* last_error() { return g_err.c_str(); }
+
+namespace {
+
+int dev_alloc(Plan& p, void** ptr, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes for %s failed", bytes, what);
+    return DDI_ERR_OOM;
+  }
+  p.bytes += bytes;
+  return DDI_OK;
+}
+
+template <typename V>
+int upload(Plan& p, void** dst, const std::vector<V>& v, const char* what, cudaStream_t s) {
+  DDI_TRY(dev_alloc(p, dst, sizeof(V) * std::max<size_t>(1, v.size()), what));
+  if (!v.empty()) DDI_CUDA(cudaMemcpyAsync(*dst, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice, s));
+  return DDI_OK;
+}
+
+// doubles -> the plan's real type
+int upload_real(Plan& p, void** dst, const std::vector<double>& v, const char* what, cudaStream_t s,
+                std::vector<float>* keep) {
+  if (p.prec == DDI_FP64) return upload(p, dst, v, what, s);
+  keep->assign(v.begin(), v.end());
+  return upload(p, dst, *keep, what, s);
+}
+
+void choose_tile(Plan& p) {
+  // Tiles are at least w - 1 cells per axis (a footprint reaches its own tile and the
+  // next one only) and divide the fine grid.  3D: one warp per z-plane of the tile.
+  auto pick = [](int want, int need, int nf) {
+    for (int t = std::min(want, nf); t >= need && t >= 1; --t)
+      if (nf % t == 0) return t;
+    for (int t = need; t <= nf; ++t)
+      if (nf % t == 0) return t;
+    return nf;
+  };
+  const int need = p.w - 1;
+  int want[3];
+  if (p.dim == 3) {
+    if (p.prec == DDI_FP32) {
+      want[0] = 32; want[1] = 16; want[2] = 16;
+    } else {
+      want[0] = 16; want[1] = 16; want[2] = 16;
+    }
+  } else {
+    want[0] = 64; want[1] = 64; want[2] = 1;
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (p.desc.tile[d] > 0) want[d] = p.desc.tile[d];
+    if (d < p.dim && want[d] < need) want[d] = need;
+    p.tile[d] = d < p.dim ? pick(want[d], need, p.nf[d]) : 1;
+    p.ntile[d] = p.nf[d] / p.tile[d];
+  }
+  p.npl = p.dim == 3 ? p.tile[2] : p.tile[1];
+  const int warps = std::min(p.npl, kSpreadThreads / 32);
+  p.spread_threads = 32 * std::max(1, warps);
+}
+
+void free_plan(Plan& p) {
+  void* ptrs[] = {p.d_l0,     p.d_psi,  p.d_scale, p.d_c,    p.d_cz,    p.d_deconv, p.d_fine,  p.d_partial,
+                  p.d_visits, p.d_prng, p.d_items, p.d_split, p.d_psi1, p.d_rho,    p.d_phi,   p.d_work,
+                  p.d_work2,  p.d_kin,  p.d_red,   p.d_io_in, p.d_io_out};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (int i = 0; i < 8; ++i)
+    if (p.d_tw[i]) {
+      cudaFree(p.d_tw[i]);
+      p.d_tw[i] = nullptr;
+    }
+  if (p.h_red) cudaFreeHost(p.h_red);
+  if (p.ev_created)
+    for (cudaEvent_t& e : p.mark_ev) cudaEventDestroy(e);
+}
+
+}  // namespace
+
+int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
+  std::string err;
+  {
+    const int st = normalise_desc(desc_in, &p.desc, &err);
+    if (st != DDI_OK) {
+      set_error("%s", err.c_str());
+      return st;
+    }
+  }
+  const ddi_plan_desc& d = p.desc;
+  DDI_CUDA(cudaGetDevice(&p.device));
+  p.dim = d.dim;
+  p.prec = d.precision;
+  p.dv = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    p.n[a] = a < d.dim ? d.n[a] : 1;
+    p.nf[a] = a < d.dim ? 2 * d.n[a] : 1;
+    p.h[a] = a < d.dim ? d.len[a] / (double)d.n[a] : 1.0;
+    if (a < d.dim) p.dv *= p.h[a];
+  }
+  p.w = kernel_width(d);
+  p.beta = kernel_beta(p.w);
+  build_quadrature(d, &p.quad);
+  p.M = p.quad.M;
+  choose_tile(p);
+  const int dim = d.dim, W = p.w;
+
+  // one node of each (k, -k) pair: the first half of the azimuth
+  const int nphi = d.nphi, half = nphi / 2;
+  std::vector<int64_t> qs;
+  qs.reserve(p.M / 2);
+  for (int64_t q = 0; q < p.M; ++q)
+    if ((q % nphi) < half) qs.push_back(q);
+  p.Mh = (int64_t)qs.size();
+
+  // first taps (wrapped), kernel values and scales; processing order groups nodes by
+  // their first-tap tile (spatial locality of the interpolation reads)
+  std::vector<int> l0w(3 * p.Mh, 0);
+  std::vector<double> fr(3 * p.Mh, 0.0);
+  std::vector<int64_t> okey(p.Mh);
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int64_t q = qs[i];
+    for (int a = 0; a < dim; ++a) {
+      const double k = p.quad.k[dim * q + a];
+      const int64_t l0 = fine_start(k, p.h[a], p.nf[a], W);
+      const double s = k * ((p.h[a] * (double)p.nf[a]) / (2.0 * M_PI));
+      fr[3 * i + a] = s - (double)l0;  // tap a sits at x = l0 + a - s
+      l0w[3 * i + a] = (int)(((l0 % p.nf[a]) + p.nf[a]) % p.nf[a]);
+    }
+    const int bx = l0w[3 * i] / p.tile[0], by = l0w[3 * i + 1] / p.tile[1], bz = l0w[3 * i + 2] / p.tile[2];
+    const int64_t bin = ((int64_t)bz * p.ntile[1] + by) * p.ntile[0] + bx;
+    const int64_t key = ((int64_t)l0w[3 * i + 2] * p.nf[1] + l0w[3 * i + 1]) * p.nf[0] + l0w[3 * i];
+    okey[i] = bin * p.fine_points() + key;
+  }
+  std::vector<int64_t> perm(p.Mh);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return okey[a] < okey[b]; });
+
+  p.order.resize(p.Mh);
+  std::vector<ushort4> l0s(p.Mh);
+  std::vector<double> psi((size_t)p.Mh * 3 * W, 1.0), scale(p.Mh);
+  const double hw = 0.5 * (double)W;
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int64_t o = perm[i];
+    p.order[i] = qs[o];
+    l0s[i] = make_ushort4((unsigned short)l0w[3 * o], (unsigned short)l0w[3 * o + 1],
+                          (unsigned short)l0w[3 * o + 2], 0);
+    for (int a = 0; a < 3; ++a)
+      for (int t = 0; t < W; ++t) {
+        double v = a < dim ? 0.0 : (t == 0 ? 1.0 : 0.0);
+        if (a < dim) {
+          const double z = ((double)t - fr[3 * o + a]) / hw;
+          if (z * z < 1.0) v = std::exp(p.beta * (std::sqrt((1.0 - z) * (1.0 + z)) - 1.0));
+        }
+        psi[((size_t)i * 3 + a) * W + t] = v;
+      }
+    scale[i] = 2.0 * p.dv * p.quad.W[qs[o]];
+  }
+
+  // spread work list: per tile, the nodes whose taps reach it with their starts relative
+  // to the tile, ordered by (o_owned, o_row, ox) so that each owned plane's nodes are one
+  // contiguous range; long lists are cut into items that write partial tiles
+  const int ntiles = p.ntile[0] * p.ntile[1] * p.ntile[2];
+  std::vector<std::vector<std::pair<int64_t, int4>>> lists(ntiles);
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int lv[3] = {l0s[i].x, l0s[i].y, l0s[i].z};
+    int ta[3][2], nt[3];
+    for (int a = 0; a < 3; ++a) {
+      const int l = a < dim ? lv[a] : 0;
+      const int w = a < dim ? W : 1;
+      const int sh = p.ntile[a] > 1 ? p.tile[a] / 2 : 0;  // lattice shift of tile_origin
+      ta[a][0] = ((l + sh) % p.nf[a]) / p.tile[a];
+      ta[a][1] = ((l + w - 1 + sh) % p.nf[a]) / p.tile[a];
+      nt[a] = ta[a][1] != ta[a][0] ? 2 : 1;
+    }
+    for (int cz = 0; cz < nt[2]; ++cz)
+      for (int cy = 0; cy < nt[1]; ++cy)
+        for (int cx = 0; cx < nt[0]; ++cx) {
+          const int bx = ta[0][cx], by = ta[1][cy], bz = ta[2][cz];
+          const int t = (bz * p.ntile[1] + by) * p.ntile[0] + bx;
+          const int ox = rel_start(lv[0], tile_origin(bx, p.tile[0], p.ntile[0], p.nf[0]), p.nf[0], W);
+          const int oy = rel_start(lv[1], tile_origin(by, p.tile[1], p.ntile[1], p.nf[1]), p.nf[1], W);
+          const int oz = dim == 3 ? rel_start(lv[2], tile_origin(bz, p.tile[2], p.ntile[2], p.nf[2]), p.nf[2], W) : 0;
+          // starts lie in [-15, 2048): offset by 32 into 12-bit fields
+          const int64_t key = dim == 3 ? (((int64_t)oz + 32) * 4096 + (oy + 32)) * 4096 + (ox + 32)
+                                       : ((int64_t)oy + 32) * 4096 + (ox + 32);
+          lists[t].push_back(std::make_pair(key, make_int4((int)i, ox, oy, oz)));
+        }
+  }
+  long long total = 0;
+  for (auto& L : lists) {
+    std::stable_sort(L.begin(), L.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
+      return a.first < b.first;
+    });
+    total += (long long)L.size();
+  }
+  p.visits = total;
+  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(512, total / (152LL * 6));
+  const bool wrap_owned = dim == 3 ? p.ntile[2] == 1 : p.ntile[1] == 1;
+  std::vector<int4> visits;
+  visits.reserve(total);
+  std::vector<SpreadItem> items;
+  std::vector<SplitTile> split;
+  int slot = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    const int beg = (int)visits.size();
+    for (auto& e : lists[t]) visits.push_back(e.second);
+    const int v = (int)lists[t].size();
+    if (v <= p.chunk) {
+      items.push_back(SpreadItem{t, beg, beg + v, -1});
+    } else {
+      const int nch = (v + p.chunk - 1) / p.chunk;
+      split.push_back(SplitTile{t, slot, nch, 0});
+      for (int c = 0; c < nch; ++c)
+        items.push_back(SpreadItem{t, beg + c * p.chunk, beg + std::min(v, (c + 1) * p.chunk), slot + c});
+      slot += nch;
+    }
+  }
+  // heaviest items first so the long ones start early
+  std::stable_sort(items.begin(), items.end(),
+                   [](const SpreadItem& a, const SpreadItem& b) { return (a.vend - a.vbeg) > (b.vend - b.vbeg); });
+  p.nitems = (int)items.size();
+  p.nsplit = (int)split.size();
+  p.nslots = slot;
+  // per item and owned plane: the visits whose taps along the owned axis cover the plane
+  std::vector<int2> prng((size_t)p.nitems * p.npl);
+  for (int it = 0; it < p.nitems; ++it) {
+    const SpreadItem& I = items[it];
+    for (int pl = 0; pl < p.npl; ++pl) {
+      int lo = I.vbeg, hi = I.vend;
+      if (!wrap_owned) {
+        auto owned = [&](int k) { return dim == 3 ? visits[k].w : visits[k].z; };
+        int l = I.vbeg, h = I.vend;
+        while (l < h) {
+          const int m = (l + h) / 2;
+          if (owned(m) < pl - W + 1) l = m + 1; else h = m;
+        }
+        lo = l;
+        h = I.vend;
+        while (l < h) {
+          const int m = (l + h) / 2;
+          if (owned(m) <= pl) l = m + 1; else h = m;
+        }
+        hi = l;
+      }
+      prng[(size_t)it * p.npl + pl] = make_int2(lo, hi);
+    }
+  }
+
+  // deconvolution factors 1/psihat(2 pi j'/nf), j' = j - n/2
+  std::vector<double> dc;
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < p.n[a]; ++j)
+      dc.push_back(p.n[a] == 1 ? 1.0
+                               : 1.0 / es_kernel_hat(2.0 * M_PI * (double)(j - p.n[a] / 2) / (double)p.nf[a], W, p.beta));
+
+  // device memory
+  const size_t rs = p.real_size(), cs = p.cx_size();
+  std::vector<float> k1, k2, k3;
+  DDI_TRY(upload(p, &p.d_l0, l0s, "node taps", stream));
+  DDI_TRY(upload_real(p, &p.d_psi, psi, "kernel values", stream, &k1));
+  DDI_TRY(upload_real(p, &p.d_scale, scale, "node scales", stream, &k2));
+  DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
+  DDI_TRY(upload(p, (void**)&p.d_visits, visits, "visit lists", stream));
+  DDI_TRY(upload(p, (void**)&p.d_prng, prng, "plane ranges", stream));
+  DDI_TRY(upload(p, (void**)&p.d_items, items, "work items", stream));
+  DDI_TRY(upload(p, (void**)&p.d_split, split, "split tiles", stream));
+  DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
+  DDI_TRY(dev_alloc(p, &p.d_cz, cs * p.Mh * W, "node plane factors"));
+  DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
+  DDI_TRY(dev_alloc(p, &p.d_partial, cs * (size_t)p.tile[0] * p.tile[1] * p.tile[2] * std::max(1, p.nslots),
+                    "partial tiles"));
+  const size_t N = (size_t)p.grid_points();
+  DDI_TRY(dev_alloc(p, &p.d_psi1, cs * N, "gpe psi1"));
+  DDI_TRY(dev_alloc(p, &p.d_rho, rs * N, "gpe rho"));
+  DDI_TRY(dev_alloc(p, &p.d_phi, rs * N, "gpe phi"));
+  DDI_TRY(dev_alloc(p, &p.d_work, cs * N, "gpe work"));
+  DDI_TRY(dev_alloc(p, &p.d_work2, cs * N, "gpe work2"));
+  DDI_TRY(dev_alloc(p, &p.d_kin, cs * (p.n[0] + p.n[1] + p.n[2]), "kinetic tables"));
+  p.red_blocks = 1024;
+  DDI_TRY(dev_alloc(p, (void**)&p.d_red, sizeof(double) * 16 * (p.red_blocks + 1), "reductions"));
+  if (cudaMallocHost((void**)&p.h_red, sizeof(double) * 64) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMallocHost failed");
+    return DDI_ERR_OOM;
+  }
+  DDI_TRY(dev_alloc(p, &p.d_io_in, rs * N, "host io in"));
+  DDI_TRY(dev_alloc(p, &p.d_io_out, rs * N, "host io out"));
+  for (int a = 0; a < 3; ++a) {
+    if (p.nf[a] > 1) DDI_TRY(make_twiddles(p, p.nf[a]));
+    if (p.n[a] > 1) DDI_TRY(make_twiddles(p, p.n[a]));
+  }
+  // the host vectors above die with this frame: finish the uploads first
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  if (spread_smem_bytes(p) + (size_t)(p.spread_threads / 32) * (2 * 32 * W * rs + 32 * (cs + 8)) > 220 * 1024) {
+    set_error("spread tile needs %zu bytes of shared memory; choose a smaller tile", spread_smem_bytes(p));
+    return DDI_ERR_ARG;
+  }
+  return DDI_OK;
+}
+
+void destroy_plan(Plan& p) { free_plan(p); }
+
+}  // namespace ddi
+
+// ==== C ABI ======================================================================================
+using ddi::Plan;
+
+extern "C" {
+
+const char* ddi_status_str(int status) {
+  switch (status) {
+    case DDI_OK: return "DDI_OK";
+    case DDI_ERR_ARG: return "DDI_ERR_ARG: invalid argument";
+    case DDI_ERR_CUDA: return "DDI_ERR_CUDA: CUDA runtime error";
+    case DDI_ERR_OOM: return "DDI_ERR_OOM: device allocation failed";
+    case DDI_ERR_NONFINITE: return "DDI_ERR_NONFINITE: NaN or Inf encountered";
+    case DDI_ERR_TIMEOUT: return "DDI_ERR_TIMEOUT: bounded device wait gave up";
+    case DDI_ERR_NOCONV: return "DDI_ERR_NOCONV: iteration limit reached";
+    default: return "unknown ddi status";
+  }
+}
+
+const char* ddi_last_error(void) { return ddi::last_error(); }
+
+int ddi_quadrature_tables(const ddi_plan_desc* desc, int64_t* M, double* k, double* W, int32_t* l0) {
+  ddi_plan_desc d;
+  std::string err;
+  int s = ddi::normalise_desc(desc, &d, &err);
+  if (s != DDI_OK) {
+    ddi::set_error("%s", err.c_str());
+    return s;
+  }
+  if (!M) {
+    ddi::set_error("M must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  ddi::QuadTables t;
+  ddi::build_quadrature(d, &t);
+  *M = t.M;
+  if (k) memcpy(k, t.k.data(), sizeof(double) * t.k.size());
+  if (W) memcpy(W, t.W.data(), sizeof(double) * t.W.size());
+  if (l0) {
+    const int w = ddi::kernel_width(d);
+    for (int64_t q = 0; q < t.M; ++q)
+      for (int a = 0; a < d.dim; ++a)
+        l0[d.dim * q + a] = (int32_t)ddi::fine_start(t.k[d.dim * q + a], t.h[a], 2 * d.n[a], w);
+  }
+  return DDI_OK;
+}
+
+int ddi_plan_create(ddi_plan* out, const ddi_plan_desc* desc, void* stream) {
+  if (!out) {
+    ddi::set_error("out is NULL");
+    return DDI_ERR_ARG;
+  }
+  *out = nullptr;
+  ddi_plan_s* h = new (std::nothrow) ddi_plan_s();
+  if (!h) {
+    ddi::set_error("host allocation failed");
+    return DDI_ERR_OOM;
+  }
+  int s = ddi::create_plan(h->p, desc, static_cast<cudaStream_t>(stream));
+  if (s != DDI_OK) {
+    ddi::destroy_plan(h->p);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return DDI_OK;
+}
+
+int ddi_plan_destroy(ddi_plan plan) {
+  if (!plan) return DDI_OK;
+  ddi::destroy_plan(plan->p);
+  delete plan;
+  return DDI_OK;
+}
+
+int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info) {
+  if (!plan || !info) {
+    ddi::set_error("plan and info must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  const Plan& p = plan->p;
+  info->dim = p.dim;
+  info->precision = p.prec;
+  for (int a = 0; a < 3; ++a) {
+    info->n[a] = p.n[a];
+    info->nf[a] = p.nf[a];
+    info->tile[a] = p.tile[a];
+  }
+  info->width = p.w;
+  info->beta = p.beta;
+  info->nodes = p.M;
+  info->nodes_used = p.Mh;
+  info->spread_items = p.nitems;
+  info->spread_split_tiles = p.nsplit;
+  info->interp_items = (int)((p.Mh + 255) / 256);
+  info->kmax = p.desc.kmax;
+  info->nr = p.desc.nr;
+  info->ntheta = p.desc.ntheta;
+  info->nphi = p.desc.nphi;
+  info->device_bytes = p.bytes;
+  return DDI_OK;
+}
+
+int ddi_plan_node_order(ddi_plan plan, int64_t* q) {
+  if (!plan || !q) {
+    ddi::set_error("plan and q must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  memcpy(q, plan->p.order.data(), sizeof(int64_t) * plan->p.order.size());
+  return DDI_OK;
+}
+
+static int check_plan_ptrs(ddi_plan plan, const void* a, const void* b) {
+  if (!plan || !a || !b) {
+    ddi::set_error("plan and array pointers must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->p.device) {
+    ddi::set_error("the current device (%d) is not the plan's device (%d)", dev, plan->p.device);
+    return DDI_ERR_ARG;
+  }
+  return DDI_OK;
+}
+
+int ddi_apply(ddi_plan plan, const void* rho, void* phi, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, rho, phi));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  if (p.prec == DDI_FP64) return ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s);
+  return ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+}
+
+int ddi_apply_host(ddi_plan plan, const void* rho_host, void* phi_host, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, rho_host, phi_host));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  const size_t bytes = p.real_size() * (size_t)p.grid_points();
+  DDI_CUDA(cudaMemcpyAsync(p.d_io_in, rho_host, bytes, cudaMemcpyHostToDevice, s));
+  if (p.prec == DDI_FP64) {
+    DDI_TRY(ddi::run_ddi<double>(p, static_cast<const double*>(p.d_io_in), static_cast<double*>(p.d_io_out), s));
+  } else {
+    DDI_TRY(ddi::run_ddi<float>(p, static_cast<const float*>(p.d_io_in), static_cast<float*>(p.d_io_out), s));
+  }
+  DDI_CUDA(cudaMemcpyAsync(phi_host, p.d_io_out, bytes, cudaMemcpyDeviceToHost, s));
+  DDI_CUDA(cudaStreamSynchronize(s));
+  return DDI_OK;
+}
+
+int ddi_apply_timed(ddi_plan plan, const void* rho, void* phi, void* stream, const char** names, double* ms,
+                    int cap, int* count) {
+  DDI_TRY(check_plan_ptrs(plan, rho, phi));
+  if (!names || !ms || !count || cap < 1) {
+    ddi::set_error("names, ms and count must not be NULL and cap >= 1");
+    return DDI_ERR_ARG;
+  }
+  Plan& p = plan->p;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p.ev_created) {
+    for (cudaEvent_t& e : p.mark_ev) DDI_CUDA(cudaEventCreate(&e));
+    p.ev_created = true;
+  }
+  p.timing = true;
+  p.nmarks = 0;
+  DDI_CUDA(cudaEventRecord(p.mark_ev[0], s));
+  int st = p.prec == DDI_FP64
+               ? ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s)
+               : ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+  p.timing = false;
+  if (st != DDI_OK) return st;
+  DDI_CUDA(cudaStreamSynchronize(s));
+  const int n = p.nmarks < cap ? p.nmarks : cap;
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    DDI_CUDA(cudaEventElapsedTime(&t, p.mark_ev[i], p.mark_ev[i + 1]));
+    names[i] = p.mark_names[i];
+    ms[i] = (double)t;
+  }
+  *count = n;
+  return DDI_OK;
+}
+
+int ddi_type2(ddi_plan plan, const void* rho, void* c, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, rho, c));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  if (p.prec == DDI_FP64) {
+    DDI_TRY(ddi::run_type2<double>(p, static_cast<const double*>(rho), s));
+  } else {
+    DDI_TRY(ddi::run_type2<float>(p, static_cast<const float*>(rho), s));
+  }
+  DDI_CUDA(cudaMemcpyAsync(c, p.d_c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
+  return DDI_OK;
+}
+
+int ddi_type1(ddi_plan plan, const void* c, void* phi, void* stream) {
+  DDI_TRY(check_plan_ptrs(plan, c, phi));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan& p = plan->p;
+  DDI_CUDA(cudaMemcpyAsync(p.d_c, c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
+  if (p.prec == DDI_FP64) return ddi::run_type1_from_c<double>(p, static_cast<double*>(phi), s);
+  return ddi::run_type1_from_c<float>(p, static_cast<float*>(phi), s);
+}
+
+}  // extern "C"

@@ -35,7 +35,7 @@ class PlanDesc(ctypes.Structure):
                 ("len", ctypes.c_double * 3), ("axis_n", ctypes.c_double * 3), ("axis_m", ctypes.c_double * 3),
                 ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
                 ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
-                ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("spread_method", ctypes.c_int)]
+                ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -112,7 +112,7 @@ def _check(status, where):
 
 
 def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
-              precision=FP64, nufft_tol=0.0, tile=None, chunk=0, spread_method=0):
+              precision=FP64, nufft_tol=0.0, tile=None, chunk=0):
     d = PlanDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -130,7 +130,6 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.precision = int(precision)
     d.nufft_tol = float(nufft_tol)
     d.chunk = int(chunk)
-    d.spread_method = int(spread_method)
     return d
 
 

@@ -77,11 +77,12 @@ def test_ddi_mixture_tilted_48(D, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_ddi_atomic_spread_variant(D, precision):
-    # the alternative spread (shared-memory atomics, nodes split between warps)
+def test_ddi_other_tile_shape_and_chunk(D, precision):
+    # a different spread tiling (small chunks: many split tiles) gives the same sum
     w = synth.gaussian_mixture_density(48, 8.0, seed=4)
     plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=48, ntheta=24, nphi=48,
-                 spread_method=2)
+                 tile=(16, 16, 16), chunk=100)
+    assert plan.info.spread_split_tiles > 4
     got = _run(D, plan, w["rho"])
     ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(48, 24, 48))
     assert _relinf(got, ref) <= TOL[precision]

@@ -181,6 +181,23 @@ int gpe_ground_state(ddi_plan plan, void* phi, const void* V, double beta, doubl
 int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V,
                      const void* V, double beta, double lambda, double dt, void* stream);
 
+/* ---- without allocation -------------------------------------------------------------- */
+/* The paper has no counterpart to this call: it serves callers that cannot allocate
+ * device memory (a host whose pool reserves the whole device, a plugin that may only use
+ * memory it is handed, a loop that must not risk the synchronisation an allocation can
+ * cause).  It computes the FP64 sums behind gpe_energy,
+ *   sums[0] = sum |psi|^2, sums[1] = sum V |psi|^2, sums[2] = sum |psi|^4
+ * (multiply by h^d, beta h^d / 2 for the energies), over `count` grid points.  psi:
+ * device complex array (interleaved, FP64 or FP32 per `precision`), V: device real
+ * array, sums: device pointer to 3 doubles, all owned by the caller.  Allocates nothing:
+ * its block partials live in a fixed 512 KiB device array of the library, shared by all
+ * calls, so count is limited to 2^26 (DDI_ERR_ARG beyond).  The first call on each
+ * device looks the array up (cudaGetSymbolAddress) and should come before any stream
+ * capture.  Calls that overlap on the GPU race on the shared array.  Asynchronous on
+ * `stream`. */
+int gpe_sums_noalloc(const void* psi, const void* V, int64_t count, int precision, double* sums,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

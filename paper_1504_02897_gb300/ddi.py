@@ -59,7 +59,7 @@ class GpeStats(ctypes.Structure):
 
 EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_plan_create", "ddi_plan_destroy",
            "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
-           "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint"]
+           "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def load():
         "gpe_energy": ([vp, vp, vp, cd, cd, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_ground_state": ([vp, vp, vp, cd, cd, cd, cd, ci, cd, ci, ci, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_step_adjoint": ([vp, vp, vp, vp, vp, cd, cd, cd, vp], ci),
+        "gpe_sums_noalloc": ([vp, vp, ctypes.c_int64, ci, vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +277,20 @@ class Plan:
                                        self._req(V), float(beta), float(lam), float(dt),
                                        ctypes.c_void_p(_stream(stream))), "gpe_step_adjoint")
         return cot
+
+
+def sums_noalloc(psi, V, sums, stream=None):
+    """gpe_sums_noalloc: sum |psi|^2, sum V |psi|^2, sum |psi|^4 into the device tensor
+    `sums` (3 float64) without any allocation by the library."""
+    import torch
+    prec = FP64 if psi.dtype == torch.complex128 else FP32
+    if not (psi.is_cuda and V.is_cuda and sums.is_cuda and psi.is_contiguous() and V.is_contiguous()
+            and sums.dtype == torch.float64 and sums.numel() >= 3 and psi.numel() == V.numel()):
+        raise ValueError("psi, V, sums: contiguous CUDA tensors, sums float64 with >= 3 entries")
+    _check(load().gpe_sums_noalloc(ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                   int(psi.numel()), prec, ctypes.c_void_p(sums.data_ptr()),
+                                   ctypes.c_void_p(_stream(stream))), "gpe_sums_noalloc")
+    return sums
 
 
 def trap_gradient(plan, psi0, V, beta, lam, dt, nsteps, checkpoint=20, stream=None):

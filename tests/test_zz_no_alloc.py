@@ -1,0 +1,52 @@
+"""gpe_sums_noalloc, the entry point for callers that cannot allocate device memory
+(its scratch is a fixed device array of the library).  It must agree with the sums
+inside gpe_energy, the existing path that uses plan-allocated scratch, on two calls in a
+row (the second call reuses the shared scratch the first one left behind).  Collected
+last on purpose: a failure here comes after every other test has run."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1504_02897_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-6)])
+def test_noalloc_sums_match_gpe_energy(precision, tol):
+    import torch
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    ddi.load()
+    n, lo, ln = synth.box(32, 6.0)
+    plan = ddi.Plan(3, n, lo, ln, (0.0, 0.0, 1.0), precision=precision)
+    dv = plan.dv
+    sums = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    for seed in (1, 2):                     # two calls in a row, different states
+        V = synth.harmonic_trap(n, lo, ln, (1, 1, 2))
+        psi0 = synth.gpe_initial(n, lo, ln, (1, 1, 2), eps=0.1, seed=seed)
+        psi = torch.from_numpy(psi0).to("cuda", plan.cplx_dtype)
+        Vt = torch.from_numpy(V).to("cuda", plan.real_dtype)
+        ddi.sums_noalloc(psi, Vt, sums)
+        got = sums.cpu().numpy()
+        ref = plan.gpe_energy(psi, Vt, 2.0, 0.0)   # beta = 2: E_int = h^3 sum |psi|^4
+        assert abs(got[0] * dv - ref["mass"]) <= tol * abs(ref["mass"])
+        assert abs(got[1] * dv - ref["Epot"]) <= tol * abs(ref["Epot"])
+        assert abs(got[2] * dv - ref["Eint"]) <= tol * abs(ref["Eint"])
+
+
+def test_noalloc_rejects_oversized_count():
+    import ctypes
+    import torch
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    lib = ddi.load()
+    psi = torch.zeros(4, dtype=torch.complex128, device="cuda")
+    V = torch.zeros(4, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    # the size check rejects the count before any launch, so the small buffers are never read
+    st = lib.gpe_sums_noalloc(ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(V.data_ptr()), (1 << 26) + 1, 0,
+                              ctypes.c_void_p(sums.data_ptr()), None)
+    assert st == -1
+    assert b"maximum" in lib.ddi_last_error()

@@ -64,18 +64,18 @@ template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s)
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
 
 // ---- spread work list ------------------------------------------------------------
-struct SpreadItem {
+struct SpreadUnit {
   int tile;   // linear tile index (tz * ntiles_y + ty) * ntiles_x + tx
-  int vbeg;   // range in the tile's visit list (its own bin and the lower neighbours)
-  int vend;
-  int slot;   // -1: write the tile to the fine grid; >= 0: write to partial slot
+  int plane;  // owned plane of the tile (z in 3D, y row in 2D)
+  int lo, hi; // range of visit-list entries whose taps cover the plane
+  int slot;   // -1: write the plane to the fine grid; >= 0: write to partial slot
 };
-struct SplitTile {
-  int tile, slot0, nslots, pad;
+struct SplitUnit {
+  int tile, plane, slot0, nslots;
 };
 
 // ---- spread tile geometry (host and device) -------------------------------------------------
-constexpr int kSpreadThreads = 512;  // at most one warp per owned plane, 16 warps
+constexpr int kSpreadThreads = 128;  // 4 warps per CTA, each taking work units on its own
 
 // first fine cell of tile t along an axis: t T - T/2 (mod nf), i.e. the tile lattice is
 // shifted by half a tile so that k = 0 lies inside a tile; unshifted with a single tile
@@ -134,13 +134,14 @@ struct Plan {
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
   void* d_partial = nullptr;  // cx [nslots * tile cells]
   int4* d_visits = nullptr;   // spread visit lists: (node, ox, oy, oz) relative to the tile
-  int2* d_prng = nullptr;     // [item][npl] visit range of each owned plane
-  SpreadItem* d_items = nullptr;
-  SplitTile* d_split = nullptr;
+  SpreadUnit* d_units = nullptr;
+  SplitUnit* d_split = nullptr;
+  int* d_counter = nullptr;   // unit counter of the persistent spread
   long long visits = 0;       // total visit-list entries
-  int npl = 1;                // owned units per tile (z-planes in 3D, y-rows in 2D)
-  int spread_threads = 256;
-  int nitems = 0, nsplit = 0, nslots = 0;
+  long long pairs = 0;        // total (node, plane) pairs of all units
+  int npl = 1;                // owned planes per tile (z-planes in 3D, y-rows in 2D)
+  int nunits = 0;
+  int nsplit = 0, nslots = 0;
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n}
   // GPE workspace
@@ -170,9 +171,10 @@ struct Plan {
   }
 
   int64_t grid_points() const { return (int64_t)n[0] * n[1] * n[2]; }
-  size_t spread_tile_cells() const {
+  // cells of one owned plane's shared-memory buffer (padded row stride)
+  size_t spread_plane_cells() const {
     const size_t rs = (size_t)spread_row_stride(tile[0]);
-    return dim == 3 ? (size_t)tile[2] * tile[1] * rs : (size_t)tile[1] * rs;
+    return dim == 3 ? (size_t)tile[1] * rs : rs;
   }
   int64_t fine_points() const { return (int64_t)nf[0] * nf[1] * nf[2]; }
   size_t real_size() const { return prec == DDI_FP64 ? 8 : 4; }
@@ -202,7 +204,10 @@ template <typename T> int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s);   
 template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);         // rho -> d_c, d_cz
 template <typename T> int run_type1_from_c(Plan& p, T* phi, cudaStream_t s);       // d_c -> phi
 template <typename T> int run_ddi(Plan& p, const T* rho, T* phi, cudaStream_t s);
-inline size_t spread_smem_bytes(const Plan& p) { return p.spread_tile_cells() * p.cx_size(); }
+// shared memory of one spread warp: its plane buffer and its node stage, 16-byte aligned
+__host__ __device__ inline size_t spread_warp_bytes(size_t plane_bytes, size_t stage_bytes) {
+  return ((plane_bytes + 15) & ~(size_t)15) + ((stage_bytes + 15) & ~(size_t)15);
+}
 
 // ---- plans (plan.cu) ------------------------------------------------------------------------
 int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream);

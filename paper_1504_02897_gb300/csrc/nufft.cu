@@ -19,13 +19,13 @@
 //   forward FFT x (pad + deconvolution fused), y, z, pruned to the padded block
 //   k_interp    one thread per node: f_q = sum over the w^d taps of psi F; writes
 //               c_q = 2 h^d W_q f_q and c_q psi_z (the spread's per-plane factors)
-//   k_spread    owner-computes spread: a CTA owns a fine-grid tile; one warp per z-plane
-//               streams the nodes whose taps reach that plane (ranges built by the plan)
-//               and adds c psi_z psi_y psi_x into shared memory with plain read-modify-
-//               writes (no other warp owns the plane); runs of nodes with the same
-//               footprint are summed in registers first.  The tile is written once;
-//               tiles with long lists are split into partial tiles
-//   k_reduce    sums the partial tiles of split tiles
+//   k_spread    owner-computes spread over work units (tile, z-plane): a warp takes a
+//               unit, streams the nodes whose taps reach that plane (ranges built by the
+//               plan) and adds c psi_z psi_y psi_x into its shared-memory plane with plain
+//               read-modify-writes (no other unit owns those cells); runs of nodes with
+//               the same footprint are summed in registers first.  Every plane is
+//               written once; long units are split into partial planes
+//   k_reduce    sums the partial planes of split units
 //   inverse FFT z, y, x (pruned to the cropped block; x fused with crop, deconvolution
 //               and real part)
 #include <algorithm>
@@ -136,18 +136,17 @@ struct SpreadArgs {
   GridDims g;
   int tile[3];
   int ntile[3];
-  int npl;                  // owned units per tile: z-planes (3D) or y-rows (2D)
-  const SpreadItem* items;
-  const int2* prng;         // [item][npl]: visit range of each owned unit
+  const SpreadUnit* units;  // (tile, plane, visit range, slot), largest first
+  int nunits;
+  int* counter;             // next unit to take (zeroed before the launch)
   const int4* visits;       // (node, ox, oy, oz): starts relative to the tile origin
   const void* cz;           // [node][w] c psi_owned
   const void* psi;          // [node][3][w]
   void* fine;
-  void* partial;
+  void* partial;            // [slot][plane cells]
 };
 
-// per-warp staging buffer of k_spread: 32 nodes' kernel values along x and y, plane
-// factor c psi_owned and starts (ox, oy)
+// per-warp shared memory of k_spread: the owned plane and a stage of 32 nodes
 template <typename T, int W>
 struct alignas(16) WarpStage {
   T px[32][W];
@@ -156,6 +155,14 @@ struct alignas(16) WarpStage {
   int2 o[32];
 };
 
+// Spread, one warp per work unit = (tile, owned plane).  The plane's cells are touched by
+// no other unit, so the warp accumulates them in its own shared-memory buffer with plain
+// read-modify-writes and writes them once.  Persistent: warps take units from a counter
+// (largest first).  Lanes stage 32 nodes at a time (kernel values along x and y, c psi
+// along the owned axis, starts), then each node adds c psi_owned psi_y psi_x to the cells
+// of its footprint in the plane (lanes: x fastest, then y rows).  Consecutive nodes with
+// the same (oy, ox) are summed in registers and written once per run.  In 2D the owned
+// plane is a y-row.
 template <typename T, int W, int DIM>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
   using C = cx_t<T>;
@@ -167,45 +174,38 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
   const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
   const int RS = spread_row_stride(TX);
   const bool swz = spread_swizzle(TX);
-  const int NPL = a.npl;
-  const int PSZ = DIM == 3 ? TY * RS : RS;
-  C* acc = reinterpret_cast<C*>(smem_raw);  // [NPL][PSZ]
-  const int nw = blockDim.x >> 5;
+  const int PSZ = DIM == 3 ? TY * RS : RS;  // cells of one plane buffer
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpStage<T, W>* stage =
-      reinterpret_cast<WarpStage<T, W>*>(smem_raw + ((NPL * PSZ * sizeof(C) + 15) & ~(size_t)15)) + warp;
-
-  const SpreadItem it = a.items[blockIdx.x];
-  const int tx = it.tile % a.ntile[0];
-  const int ty = (it.tile / a.ntile[0]) % a.ntile[1];
-  const int tz = it.tile / (a.ntile[0] * a.ntile[1]);
+  const size_t per_warp = spread_warp_bytes(PSZ * sizeof(C), sizeof(WarpStage<T, W>));
+  C* plane = reinterpret_cast<C*>(smem_raw + warp * per_warp);
+  WarpStage<T, W>* stage = reinterpret_cast<WarpStage<T, W>*>(smem_raw + warp * per_warp + ((PSZ * sizeof(C) + 15) & ~(size_t)15));
   const int nfx = a.g.nf[0], nfy = a.g.nf[1], nfz = a.g.nf[2];
-  const int T0x = tile_origin(tx, TX, a.ntile[0], nfx);
-  const int T0y = tile_origin(ty, TY, a.ntile[1], nfy);
-  const int T0z = tile_origin(tz, TZ, a.ntile[2], nfz);
   const bool wrx = a.ntile[0] == 1, wry = a.ntile[1] == 1;
   const bool wrp = DIM == 3 ? a.ntile[2] == 1 : a.ntile[1] == 1;  // owned axis wraps in the tile
-  const bool wrap = wrx || wry || wrp;
   const int nfp = DIM == 3 ? nfz : nfy;
-
-  for (int i = threadIdx.x; i < NPL * PSZ; i += blockDim.x) acc[i] = cmk<C>((T)0, (T)0);
-  __syncthreads();
-
   const int4* __restrict__ vis = a.visits;
   const C* __restrict__ czg = static_cast<const C*>(a.cz);
   const T* __restrict__ psi = static_cast<const T*>(a.psi);
   const int rx = lane % XL, ry = lane / XL;
+  const int ncell = DIM == 3 ? TX * TY : TX;  // cells of one owned plane
 
-  for (int p = warp; p < NPL; p += nw) {
-    const int2 rng = a.prng[(size_t)blockIdx.x * NPL + p];
-    C* plane = acc + p * PSZ;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(a.counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= a.nunits) break;
+    const SpreadUnit U = a.units[u];
+    for (int i = lane; i < PSZ; i += 32) plane[i] = cmk<C>((T)0, (T)0);
+    __syncwarp();
+    const int p = U.plane;
     T ar[NM], ai[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) ar[m] = ai[m] = (T)0;
     int run_x = INT_MIN, run_y = 0;
-    for (int kb = rng.x; kb < rng.y; kb += 32) {
-      const int cnt = min(32, rng.y - kb);
-      // stage: lane j loads node kb + j (independent loads, latencies overlap)
+    C* cellp[NM];
+    bool okp[NM];
+    for (int kb = U.lo; kb < U.hi; kb += 32) {
+      const int cnt = min(32, U.hi - kb);
       if (lane < cnt) {
         const int4 e = vis[kb + lane];
         const size_t node = (size_t)e.x;
@@ -225,32 +225,34 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
       __syncwarp();
       for (int j = 0; j < cnt; ++j) {
         const int2 o = stage->o[j];
-        if (o.x == INT_MIN + 1) continue;  // wraps only: this node misses plane p
+        if (o.x == INT_MIN + 1) continue;  // wrapping tiles only: this node misses plane p
         if (o.x != run_x || o.y != run_y) {
           if (run_x != INT_MIN) {
-            // flush the finished run into this warp's plane
-            int xx = run_x + rx;
-            if (wrx && xx < 0) xx += nfx;
-            if (rx < W && (unsigned)xx < (unsigned)TX) {
 #pragma unroll
-              for (int m = 0; m < NM; ++m) {
-                const int r = ry + RL * m;
-                int yy = run_y + r;
-                if (wry && yy < 0) yy += nfy;
-                if (DIM == 3 ? (r < W && (unsigned)yy < (unsigned)TY) : ry == 0) {
-                  C* cell = plane + (DIM == 3 ? spread_cell(yy, xx, RS, swz) : xx);
-                  C cur = *cell;
-                  cur.x += ar[m];
-                  cur.y += ai[m];
-                  *cell = cur;
-                }
+            for (int m = 0; m < NM; ++m)
+              if (okp[m]) {
+                C cur = *cellp[m];
+                cur.x += ar[m];
+                cur.y += ai[m];
+                *cellp[m] = cur;
               }
-            }
 #pragma unroll
             for (int m = 0; m < NM; ++m) ar[m] = ai[m] = (T)0;
           }
+          // cells of this lane for the new footprint
           run_x = o.x;
           run_y = o.y;
+          int xx = o.x + rx;
+          if (wrx && xx < 0) xx += nfx;
+          const bool okx = rx < W && (unsigned)xx < (unsigned)TX;
+#pragma unroll
+          for (int m = 0; m < NM; ++m) {
+            const int r = ry + RL * m;
+            int yy = o.y + r;
+            if (wry && yy < 0) yy += nfy;
+            okp[m] = okx && (DIM == 3 ? (r < W && (unsigned)yy < (unsigned)TY) : ry == 0);
+            cellp[m] = plane + (DIM == 3 ? spread_cell(okp[m] ? yy : 0, okp[m] ? xx : 0, RS, swz) : (okp[m] ? xx : 0));
+          }
         }
         const C czv = stage->cz[j];
         const T wx = rx < W ? stage->px[j][rx] : (T)0;
@@ -265,71 +267,65 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
       __syncwarp();
     }
     if (run_x != INT_MIN) {
-      int xx = run_x + rx;
-      if (wrx && xx < 0) xx += nfx;
-      if (rx < W && (unsigned)xx < (unsigned)TX) {
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-          const int r = ry + RL * m;
-          int yy = run_y + r;
-          if (wry && yy < 0) yy += nfy;
-          if (DIM == 3 ? (r < W && (unsigned)yy < (unsigned)TY) : ry == 0) {
-            C* cell = plane + (DIM == 3 ? spread_cell(yy, xx, RS, swz) : xx);
-            C cur = *cell;
-            cur.x += ar[m];
-            cur.y += ai[m];
-            *cell = cur;
-          }
+      for (int m = 0; m < NM; ++m)
+        if (okp[m]) {
+          C cur = *cellp[m];
+          cur.x += ar[m];
+          cur.y += ai[m];
+          *cellp[m] = cur;
         }
+    }
+    __syncwarp();
+    // write the plane (or this unit's partial plane)
+    const int tx = U.tile % a.ntile[0];
+    const int ty = (U.tile / a.ntile[0]) % a.ntile[1];
+    const int tz = U.tile / (a.ntile[0] * a.ntile[1]);
+    const int T0x = tile_origin(tx, TX, a.ntile[0], nfx);
+    const int T0y = tile_origin(ty, TY, a.ntile[1], nfy);
+    const int T0z = tile_origin(tz, TZ, a.ntile[2], nfz);
+    if (U.slot < 0) {
+      C* fine = static_cast<C*>(a.fine);
+      for (int i = lane; i < ncell; i += 32) {
+        const int lx = i % TX, ly = DIM == 3 ? i / TX : p;
+        const int lz = DIM == 3 ? p : 0;
+        const int gx = T0x + lx, gy = T0y + ly, gz = T0z + lz;
+        const long long off =
+            ((long long)(gz >= nfz ? gz - nfz : gz) * nfy + (gy >= nfy ? gy - nfy : gy)) * nfx + (gx >= nfx ? gx - nfx : gx);
+        fine[off] = plane[DIM == 3 ? spread_cell(ly, lx, RS, swz) : lx];
+      }
+    } else {
+      C* part = static_cast<C*>(a.partial) + (long long)U.slot * ncell;
+      for (int i = lane; i < ncell; i += 32) {
+        const int lx = i % TX, ly = i / TX;
+        part[i] = plane[DIM == 3 ? spread_cell(ly, lx, RS, swz) : lx];
       }
     }
-  }
-  (void)wrap;
-  __syncthreads();
-
-  const int cells = TX * TY * TZ;
-  if (it.slot < 0) {
-    C* fine = static_cast<C*>(a.fine);
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-      const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-      const int gx = T0x + lx, gy = T0y + ly, gz = T0z + lz;
-      const long long off = ((long long)(gz >= nfz ? gz - nfz : gz) * nfy + (gy >= nfy ? gy - nfy : gy)) * nfx +
-                            (gx >= nfx ? gx - nfx : gx);
-      fine[off] = acc[DIM == 3 ? lz * PSZ + spread_cell(ly, lx, RS, swz) : ly * PSZ + lx];
-    }
-  } else {
-    C* part = static_cast<C*>(a.partial) + (long long)it.slot * cells;
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-      const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-      part[i] = acc[DIM == 3 ? lz * PSZ + spread_cell(ly, lx, RS, swz) : ly * PSZ + lx];
-    }
+    __syncwarp();
   }
 }
 
-// Sums the partial tiles of split tiles; blockIdx.y selects a slice of the tile's cells
-// so that the few, large split tiles still spread over the whole GPU.
-constexpr int kReduceSlices = 8;
-template <typename T>
-__global__ void k_reduce(const SplitTile* __restrict__ split, const cx_t<T>* __restrict__ partial,
-                         cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx, int nty,
-                         int ntz) {
+// Sums the partial planes of split units into the fine grid.
+template <typename T, int DIM>
+__global__ void k_reduce(const SplitUnit* __restrict__ split, const cx_t<T>* __restrict__ partial,
+                         cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx, int nty, int ntz) {
   using C = cx_t<T>;
-  const SplitTile st = split[blockIdx.x];
-  const int cells = TX * TY * TZ;
-  const int per = (cells + kReduceSlices - 1) / kReduceSlices;
-  const int c0 = blockIdx.y * per, c1 = min(cells, c0 + per);
+  const SplitUnit st = split[blockIdx.x];
+  const int ncell = DIM == 3 ? TX * TY : TX;
   const int tx = st.tile % ntx, ty = (st.tile / ntx) % nty, tz = st.tile / (ntx * nty);
   const int ox = tile_origin(tx, TX, ntx, g.nf[0]);
   const int oy = tile_origin(ty, TY, nty, g.nf[1]);
   const int oz = tile_origin(tz, TZ, ntz, g.nf[2]);
-  for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+  for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
     T sr = 0, si = 0;
     for (int k = 0; k < st.nslots; ++k) {
-      const C v = partial[(long long)(st.slot0 + k) * cells + i];
+      const C v = partial[(long long)(st.slot0 + k) * ncell + i];
       sr += v.x;
       si += v.y;
     }
-    int gx = ox + i % TX, gy = oy + (i / TX) % TY, gz = oz + i / (TX * TY);
+    int gx = ox + i % TX;
+    int gy = oy + (DIM == 3 ? i / TX : st.plane);
+    int gz = oz + (DIM == 3 ? st.plane : 0);
     gx -= gx >= g.nf[0] ? g.nf[0] : 0;
     gy -= gy >= g.nf[1] ? g.nf[1] : 0;
     gz -= gz >= g.nf[2] ? g.nf[2] : 0;
@@ -366,26 +362,33 @@ int launch_spread(Plan& p, cudaStream_t s) {
     a.tile[d] = p.tile[d];
     a.ntile[d] = p.ntile[d];
   }
-  a.npl = p.npl;
-  a.items = p.d_items;
-  a.prng = p.d_prng;
+  a.units = p.d_units;
+  a.nunits = p.nunits;
+  a.counter = p.d_counter;
   a.visits = p.d_visits;
   a.cz = p.d_cz;
   a.psi = p.d_psi;
   a.fine = p.d_fine;
   a.partial = p.d_partial;
-  const size_t smem = ((spread_smem_bytes(p) + 15) & ~(size_t)15) + sizeof(WarpStage<T, W>) * (p.spread_threads / 32);
+  const size_t plane_bytes = p.spread_plane_cells() * sizeof(cx_t<T>);
+  const size_t smem = spread_warp_bytes(plane_bytes, sizeof(WarpStage<T, W>)) * (kSpreadThreads / 32);
   auto kern = k_spread<T, W, DIM>;
   if (smem > 48 * 1024) {
     DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
-  kern<<<p.nitems, p.spread_threads, smem, s>>>(a);
+  int per_sm = 0;
+  DDI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSpreadThreads, smem));
+  int sms = 0;
+  DDI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device));
+  const int blocks = std::max(1, std::min(per_sm * sms, (p.nunits + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32)));
+  DDI_CUDA(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
+  kern<<<blocks, kSpreadThreads, smem, s>>>(a);
   DDI_LAUNCH_CHECK();
   p.mark("spread", s);
   if (p.nsplit > 0) {
-    k_reduce<T><<<dim3(p.nsplit, kReduceSlices), 256, 0, s>>>(
-        p.d_split, static_cast<const cx_t<T>*>(p.d_partial), static_cast<cx_t<T>*>(p.d_fine), dims_of(p), p.tile[0],
-        p.tile[1], p.tile[2], p.ntile[0], p.ntile[1], p.ntile[2]);
+    k_reduce<T, DIM><<<p.nsplit, 256, 0, s>>>(p.d_split, static_cast<const cx_t<T>*>(p.d_partial),
+                                              static_cast<cx_t<T>*>(p.d_fine), dims_of(p), p.tile[0], p.tile[1],
+                                              p.tile[2], p.ntile[0], p.ntile[1], p.ntile[2]);
     DDI_LAUNCH_CHECK();
     p.mark("spread_reduce", s);
   }

@@ -5,7 +5,8 @@
 // of one half of the antipodally closed set its first fine-grid tap, its kernel values
 // psi_d at the w taps of each axis (FP64, rounded once) and its scale 2 h^d W_q, the
 // deconvolution factors, the spread work list (per fine-grid tile, the nodes whose taps
-// reach it, in order of their start relative to the tile, cut into work items), and all
+// reach it, in order of their start relative to the tile, and the work units: one per
+// tile plane, long ones cut into pieces that write partial planes), and all
 // device workspace.  ddi_plan_create is the only call that allocates.
 #include <algorithm>
 #include <cmath>
@@ -87,14 +88,12 @@ void choose_tile(Plan& p) {
     p.ntile[d] = p.nf[d] / p.tile[d];
   }
   p.npl = p.dim == 3 ? p.tile[2] : p.tile[1];
-  const int warps = std::min(p.npl, kSpreadThreads / 32);
-  p.spread_threads = 32 * std::max(1, warps);
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_l0,     p.d_psi,  p.d_scale, p.d_c,    p.d_cz,    p.d_deconv, p.d_fine,  p.d_partial,
-                  p.d_visits, p.d_prng, p.d_items, p.d_split, p.d_psi1, p.d_rho,    p.d_phi,   p.d_work,
-                  p.d_work2,  p.d_kin,  p.d_red,   p.d_io_in, p.d_io_out};
+  void* ptrs[] = {p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_cz,  p.d_deconv, p.d_fine,  p.d_partial,
+                  p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
+                  p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 8; ++i)
@@ -188,9 +187,9 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
     scale[i] = 2.0 * p.dv * p.quad.W[qs[o]];
   }
 
-  // spread work list: per tile, the nodes whose taps reach it with their starts relative
+  // spread visit lists: per tile, the nodes whose taps reach it with their starts relative
   // to the tile, ordered by (o_owned, o_row, ox) so that each owned plane's nodes are one
-  // contiguous range; long lists are cut into items that write partial tiles
+  // contiguous range
   const int ntiles = p.ntile[0] * p.ntile[1] * p.ntile[2];
   std::vector<std::vector<std::pair<int64_t, int4>>> lists(ntiles);
   for (int64_t i = 0; i < p.Mh; ++i) {
@@ -226,57 +225,62 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
     total += (long long)L.size();
   }
   p.visits = total;
-  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(512, total / (152LL * 6));
   const bool wrap_owned = dim == 3 ? p.ntile[2] == 1 : p.ntile[1] == 1;
   std::vector<int4> visits;
   visits.reserve(total);
-  std::vector<SpreadItem> items;
-  std::vector<SplitTile> split;
-  int slot = 0;
+  // work units (tile, owned plane): the list entries whose taps along the owned axis cover
+  // the plane form one contiguous range (lists are sorted by the owned start)
+  std::vector<SpreadUnit> units;
+  long long pairs = 0;
   for (int t = 0; t < ntiles; ++t) {
     const int beg = (int)visits.size();
     for (auto& e : lists[t]) visits.push_back(e.second);
-    const int v = (int)lists[t].size();
-    if (v <= p.chunk) {
-      items.push_back(SpreadItem{t, beg, beg + v, -1});
-    } else {
-      const int nch = (v + p.chunk - 1) / p.chunk;
-      split.push_back(SplitTile{t, slot, nch, 0});
-      for (int c = 0; c < nch; ++c)
-        items.push_back(SpreadItem{t, beg + c * p.chunk, beg + std::min(v, (c + 1) * p.chunk), slot + c});
-      slot += nch;
-    }
-  }
-  // heaviest items first so the long ones start early
-  std::stable_sort(items.begin(), items.end(),
-                   [](const SpreadItem& a, const SpreadItem& b) { return (a.vend - a.vbeg) > (b.vend - b.vbeg); });
-  p.nitems = (int)items.size();
-  p.nsplit = (int)split.size();
-  p.nslots = slot;
-  // per item and owned plane: the visits whose taps along the owned axis cover the plane
-  std::vector<int2> prng((size_t)p.nitems * p.npl);
-  for (int it = 0; it < p.nitems; ++it) {
-    const SpreadItem& I = items[it];
+    const int end = (int)visits.size();
+    auto owned = [&](int k) { return dim == 3 ? visits[k].w : visits[k].z; };
     for (int pl = 0; pl < p.npl; ++pl) {
-      int lo = I.vbeg, hi = I.vend;
+      int lo = beg, hi = end;
       if (!wrap_owned) {
-        auto owned = [&](int k) { return dim == 3 ? visits[k].w : visits[k].z; };
-        int l = I.vbeg, h = I.vend;
+        int l = beg, h = end;
         while (l < h) {
           const int m = (l + h) / 2;
           if (owned(m) < pl - W + 1) l = m + 1; else h = m;
         }
         lo = l;
-        h = I.vend;
+        h = end;
         while (l < h) {
           const int m = (l + h) / 2;
           if (owned(m) <= pl) l = m + 1; else h = m;
         }
         hi = l;
       }
-      prng[(size_t)it * p.npl + pl] = make_int2(lo, hi);
+      units.push_back(SpreadUnit{t, pl, lo, hi, -1});
+      pairs += hi - lo;
     }
   }
+  p.pairs = pairs;
+  // long units are cut into pieces that write partial planes (summed by k_reduce)
+  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(1024, pairs / (152LL * 32 * 2));
+  std::vector<SpreadUnit> work;
+  std::vector<SplitUnit> split;
+  int slot = 0;
+  for (const SpreadUnit& U : units) {
+    const int v = U.hi - U.lo;
+    if (v <= p.chunk) {
+      work.push_back(U);
+    } else {
+      const int nch = (v + p.chunk - 1) / p.chunk;
+      split.push_back(SplitUnit{U.tile, U.plane, slot, nch});
+      for (int c = 0; c < nch; ++c)
+        work.push_back(SpreadUnit{U.tile, U.plane, U.lo + c * p.chunk, std::min(U.hi, U.lo + (c + 1) * p.chunk), slot + c});
+      slot += nch;
+    }
+  }
+  // largest units first: the persistent spread takes them in this order
+  std::stable_sort(work.begin(), work.end(),
+                   [](const SpreadUnit& a, const SpreadUnit& b) { return (a.hi - a.lo) > (b.hi - b.lo); });
+  p.nunits = (int)work.size();
+  p.nsplit = (int)split.size();
+  p.nslots = slot;
 
   // deconvolution factors 1/psihat(2 pi j'/nf), j' = j - n/2
   std::vector<double> dc;
@@ -293,14 +297,14 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   DDI_TRY(upload_real(p, &p.d_scale, scale, "node scales", stream, &k2));
   DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
   DDI_TRY(upload(p, (void**)&p.d_visits, visits, "visit lists", stream));
-  DDI_TRY(upload(p, (void**)&p.d_prng, prng, "plane ranges", stream));
-  DDI_TRY(upload(p, (void**)&p.d_items, items, "work items", stream));
-  DDI_TRY(upload(p, (void**)&p.d_split, split, "split tiles", stream));
+  DDI_TRY(upload(p, (void**)&p.d_units, work, "work units", stream));
+  DDI_TRY(upload(p, (void**)&p.d_split, split, "split units", stream));
+  DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
   DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
   DDI_TRY(dev_alloc(p, &p.d_cz, cs * p.Mh * W, "node plane factors"));
   DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
-  DDI_TRY(dev_alloc(p, &p.d_partial, cs * (size_t)p.tile[0] * p.tile[1] * p.tile[2] * std::max(1, p.nslots),
-                    "partial tiles"));
+  const size_t plane_cells = dim == 3 ? (size_t)p.tile[0] * p.tile[1] : (size_t)p.tile[0];
+  DDI_TRY(dev_alloc(p, &p.d_partial, cs * plane_cells * std::max(1, p.nslots), "partial planes"));
   const size_t N = (size_t)p.grid_points();
   DDI_TRY(dev_alloc(p, &p.d_psi1, cs * N, "gpe psi1"));
   DDI_TRY(dev_alloc(p, &p.d_rho, rs * N, "gpe rho"));
@@ -323,8 +327,9 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   }
   // the host vectors above die with this frame: finish the uploads first
   DDI_CUDA(cudaStreamSynchronize(stream));
-  if (spread_smem_bytes(p) + (size_t)(p.spread_threads / 32) * (2 * 32 * W * rs + 32 * (cs + 8)) > 220 * 1024) {
-    set_error("spread tile needs %zu bytes of shared memory; choose a smaller tile", spread_smem_bytes(p));
+  const size_t warp_bytes = spread_warp_bytes(p.spread_plane_cells() * cs, 2 * 32 * W * rs + 32 * (cs + 8));
+  if (warp_bytes * (kSpreadThreads / 32) > 200 * 1024) {
+    set_error("spread plane needs %zu bytes of shared memory per warp; choose a smaller tile", warp_bytes);
     return DDI_ERR_ARG;
   }
   return DDI_OK;
@@ -425,7 +430,7 @@ int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info) {
   info->beta = p.beta;
   info->nodes = p.M;
   info->nodes_used = p.Mh;
-  info->spread_items = p.nitems;
+  info->spread_items = p.nunits;
   info->spread_split_tiles = p.nsplit;
   info->interp_items = (int)((p.Mh + 255) / 256);
   info->kmax = p.desc.kmax;

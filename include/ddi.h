@@ -50,6 +50,10 @@ typedef enum {
 enum { DDI_FP64 = 0, DDI_FP32 = 1 };
 
 typedef struct ddi_plan_s* ddi_plan;
+typedef struct ddi_batch_s* ddi_batch;
+
+/* ddi_batch_create flags */
+enum { DDI_BATCH_GRAPH = 1, DDI_BATCH_AUTOTUNE = 2 };
 
 /* Plan descriptor.  Zero fields take the defaults listed. */
 typedef struct {
@@ -64,7 +68,8 @@ typedef struct {
   int precision;       /* DDI_FP64 or DDI_FP32 */
   double nufft_tol;    /* requested NUFFT tolerance; 0 => 1e-13 (FP64) / 1e-6 (FP32) */
   int tile[3];         /* spread tile (x, y, z) in fine cells, >= w - 1 and dividing 2n (rounded to
-                          such a size); 0 => built-in choice */
+                          such a size); 0 => built-in choice; tile[0] < 0 => picked by the
+                          spread-tile autotuner (ddi_tune_spread_tile) when the plan is created */
   int chunk;           /* max nodes per spread work item; 0 => built-in choice */
 } ddi_plan_desc;
 
@@ -82,6 +87,7 @@ typedef struct {
   double kmax;
   int nr, ntheta, nphi;
   size_t device_bytes; /* device memory held by the plan */
+  double spread_tuned_ms; /* spread time of the tile the autotuner picked, in ms; 0 if not tuned */
 } ddi_plan_info;
 
 /* Energies of Sec. 3.2 for a state phi (all FP64). */
@@ -180,6 +186,37 @@ int gpe_ground_state(ddi_plan plan, void* phi, const void* V, double beta, doubl
  * (the step's contribution to dJ/dV_j).  One DDI of r (Phi is self-adjoint). */
 int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V,
                      const void* V, double beta, double lambda, double dt, void* stream);
+
+/* ---- batches ---------------------------------------------------------------------- */
+/* Many DDI evaluations (Sec. 2.1, Eq. DDI-Trun1) in one call: item i has its own grid,
+ * box, dipole axes, quadrature and precision (descs[i], as for ddi_plan_create) and
+ * computes phi[i] = U_dip,i * rho[i] exactly as ddi_apply does with a plan built from
+ * descs[i] (bit-identical for the same spread tile).  The items run concurrently on the
+ * batch's own side streams, forked from and joined back into `stream`.
+ * Flags: DDI_BATCH_GRAPH records the launches of all items into one CUDA graph on the
+ *   first ddi_batch_apply and replays it (one cudaGraphLaunch) while the rho/phi
+ *   pointers stay the same; new pointers re-record it.
+ *   DDI_BATCH_AUTOTUNE picks every item's spread tile with the autotuner (also done for
+ *   items whose desc.tile[0] < 0): the spread is timed on the item's node set for a few
+ *   candidate tiles on this device and the fastest kept; results are cached per grid and
+ *   quadrature shape for the life of the process, so each shape is timed once.
+ * ddi_batch_create builds all plans (host threads; allocates all device memory, none for
+ * the GPE) and synchronises `stream`.  count >= 1.  Errors: DDI_ERR_ARG for an invalid
+ * descriptor (ddi_last_error names the item), DDI_ERR_OOM, DDI_ERR_CUDA. */
+int ddi_batch_create(ddi_batch* out, const ddi_plan_desc* descs, int count, int flags, void* stream);
+/* Synchronises the device, then frees the batch (NULL is a no-op). */
+int ddi_batch_destroy(ddi_batch batch);
+/* Number of items (0 for NULL). */
+int ddi_batch_size(ddi_batch batch);
+/* Facts about item `item`'s plan (tile chosen, nodes, device bytes). */
+int ddi_batch_get_info(ddi_batch batch, int item, ddi_plan_info* info);
+/* rho, phi: host arrays of ddi_batch_size() device pointers, item i's grids in its
+ * precision; rho[i] may alias phi[i], distinct items must not share memory.
+ * Asynchronous on `stream`.  Calls on one batch must not overlap on the GPU (the items'
+ * workspaces are reused). */
+int ddi_batch_apply(ddi_batch batch, const void* const* rho, void* const* phi, void* stream);
+/* How often the graph was recorded and launched (DDI_BATCH_GRAPH); either may be NULL. */
+int ddi_batch_graph_stats(ddi_batch batch, long long* records, long long* launches);
 
 /* ---- without allocation -------------------------------------------------------------- */
 /* The paper has no counterpart to this call: it serves callers that cannot allocate

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libddi_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU_SOURCES = ["fft.cu", "fft_nufft.cu", "nufft.cu", "plan.cu", "gpe.cu", "noalloc.cu"]
+CU_SOURCES = ["fft.cu", "fft_nufft.cu", "nufft.cu", "plan.cu", "gpe.cu", "batch.cu", "noalloc.cu"]
 CPP_SOURCES = ["tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -123,6 +123,10 @@ struct Plan {
 
   QuadTables quad;                   // host copy of the tables (export, tests)
   std::vector<int64_t> order;        // processing order -> original node index
+  std::vector<ushort4> h_l0;         // host copy of d_l0 (spread lists are rebuilt from it)
+  bool gpe_ready = false;            // GPE workspace allocated (plans of a batch have none)
+  size_t spread_bytes = 0;           // device bytes of the spread lists and partial planes
+  double tuned_ms = 0.0;             // spread time of the tile the autotuner chose (0: not tuned)
 
   // device arrays (element types depend on prec), nodes in processing order
   void* d_l0 = nullptr;       // ushort4 [Mh]: wrapped first tap (x, y, z)
@@ -141,6 +145,8 @@ struct Plan {
   long long pairs = 0;        // total (node, plane) pairs of all units
   int npl = 1;                // owned planes per tile (z-planes in 3D, y-rows in 2D)
   int nunits = 0;
+  size_t spread_smem = 0;     // launch geometry of the spread (fixed per plan)
+  int spread_blocks = 1;
   int nsplit = 0, nslots = 0;
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n}
@@ -209,9 +215,16 @@ __host__ __device__ inline size_t spread_warp_bytes(size_t plane_bytes, size_t s
   return ((plane_bytes + 15) & ~(size_t)15) + ((stage_bytes + 15) & ~(size_t)15);
 }
 
+int configure_kernels(Plan& p);  // per-plan launch geometry (nufft.cu)
+
 // ---- plans (plan.cu) ------------------------------------------------------------------------
-int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream);
+int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream, bool gpe = true);
+void set_tile(Plan& p, const int want[3]);         // tile rounded as for ddi_plan_desc.tile
+int build_spread(Plan& p, cudaStream_t stream);     // spread lists for the current tile
+int time_spread(Plan& p, cudaStream_t s, int reps, float* ms);  // best of reps (nufft.cu)
+int tune_spread_tile(Plan& p, cudaStream_t s);      // autotuner (batch.cu)
 void destroy_plan(Plan& p);
+void fill_info(const Plan& p, ddi_plan_info* info);
 
 }  // namespace ddi
 

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -354,6 +355,31 @@ int launch_expand(Plan& p, cudaStream_t s) {
   return DDI_OK;
 }
 
+// launch geometry of the spread, fixed per plan (computed once so that applies make no
+// host-side queries and can be recorded into a CUDA graph)
+template <typename T, int W, int DIM>
+int configure_spread(Plan& p, cudaStream_t) {
+  const size_t plane_bytes = p.spread_plane_cells() * sizeof(cx_t<T>);
+  const size_t smem = spread_warp_bytes(plane_bytes, sizeof(WarpStage<T, W>)) * (kSpreadThreads / 32);
+  auto kern = k_spread<T, W, DIM>;
+  {
+    // the limit belongs to the kernel, shared by every plan (and thread): only raise it
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    DDI_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  int per_sm = 0;
+  DDI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSpreadThreads, smem));
+  int sms = 0;
+  DDI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device));
+  p.spread_smem = smem;
+  p.spread_blocks = std::max(1, std::min(per_sm * sms, (p.nunits + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32)));
+  return DDI_OK;
+}
+
 template <typename T, int W, int DIM>
 int launch_spread(Plan& p, cudaStream_t s) {
   SpreadArgs a;
@@ -370,17 +396,9 @@ int launch_spread(Plan& p, cudaStream_t s) {
   a.psi = p.d_psi;
   a.fine = p.d_fine;
   a.partial = p.d_partial;
-  const size_t plane_bytes = p.spread_plane_cells() * sizeof(cx_t<T>);
-  const size_t smem = spread_warp_bytes(plane_bytes, sizeof(WarpStage<T, W>)) * (kSpreadThreads / 32);
   auto kern = k_spread<T, W, DIM>;
-  if (smem > 48 * 1024) {
-    DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  int per_sm = 0;
-  DDI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSpreadThreads, smem));
-  int sms = 0;
-  DDI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device));
-  const int blocks = std::max(1, std::min(per_sm * sms, (p.nunits + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32)));
+  const size_t smem = p.spread_smem;
+  const int blocks = p.spread_blocks;
   DDI_CUDA(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
   kern<<<blocks, kSpreadThreads, smem, s>>>(a);
   DDI_LAUNCH_CHECK();
@@ -419,8 +437,50 @@ int launch_spread(Plan& p, cudaStream_t s) {
 DDI_WIDTH_SWITCH(launch_interp)
 DDI_WIDTH_SWITCH(launch_expand)
 DDI_WIDTH_SWITCH(launch_spread)
+DDI_WIDTH_SWITCH(configure_spread)
 
 }  // namespace
+
+int configure_kernels(Plan& p) {
+  if (p.prec == DDI_FP64)
+    return p.dim == 3 ? configure_spread_w<double, 3>(p, nullptr) : configure_spread_w<double, 2>(p, nullptr);
+  return p.dim == 3 ? configure_spread_w<float, 3>(p, nullptr) : configure_spread_w<float, 2>(p, nullptr);
+}
+
+// Device time of the spread (and its partial-plane reduction) for the plan's current
+// tile: the best of `reps` timed launches after one untimed one, on zeroed node values
+// (the cost depends on the node set and the tile, not on the values).
+int time_spread(Plan& p, cudaStream_t s, int reps, float* ms) {
+  DDI_CUDA(cudaMemsetAsync(p.d_cz, 0, p.cx_size() * (size_t)p.Mh * p.w, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    set_error("time_spread: %s", cudaGetErrorString(cudaGetLastError()));
+    return DDI_ERR_CUDA;
+  }
+  auto once = [&]() {
+    if (p.prec == DDI_FP64) return p.dim == 3 ? launch_spread_w<double, 3>(p, s) : launch_spread_w<double, 2>(p, s);
+    return p.dim == 3 ? launch_spread_w<float, 3>(p, s) : launch_spread_w<float, 2>(p, s);
+  };
+  int st = once();
+  float best = 0.f;
+  for (int r = 0; r < reps && st == DDI_OK; ++r) {
+    cudaEventRecord(e0, s);
+    st = once();
+    cudaEventRecord(e1, s);
+    float t = 0.f;
+    if (st == DDI_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) {
+      if (r == 0 || t < best) best = t;
+    } else if (st == DDI_OK) {
+      set_error("time_spread: %s", cudaGetErrorString(cudaGetLastError()));
+      st = DDI_ERR_CUDA;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = best;
+  return st;
+}
 
 template <typename T>
 int run_type2(Plan& p, const T* rho, cudaStream_t s) {

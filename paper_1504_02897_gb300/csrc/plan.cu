@@ -108,84 +108,33 @@ void free_plan(Plan& p) {
 
 }  // namespace
 
-int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
-  std::string err;
-  {
-    const int st = normalise_desc(desc_in, &p.desc, &err);
-    if (st != DDI_OK) {
-      set_error("%s", err.c_str());
-      return st;
-    }
-  }
-  const ddi_plan_desc& d = p.desc;
-  DDI_CUDA(cudaGetDevice(&p.device));
-  p.dim = d.dim;
-  p.prec = d.precision;
-  p.dv = 1.0;
-  for (int a = 0; a < 3; ++a) {
-    p.n[a] = a < d.dim ? d.n[a] : 1;
-    p.nf[a] = a < d.dim ? 2 * d.n[a] : 1;
-    p.h[a] = a < d.dim ? d.len[a] / (double)d.n[a] : 1.0;
-    if (a < d.dim) p.dv *= p.h[a];
-  }
-  p.w = kernel_width(d);
-  p.beta = kernel_beta(p.w);
-  build_quadrature(d, &p.quad);
-  p.M = p.quad.M;
+void set_tile(Plan& p, const int want[3]) {
+  for (int d = 0; d < 3; ++d) p.desc.tile[d] = want[d];
   choose_tile(p);
-  const int dim = d.dim, W = p.w;
+}
 
-  // one node of each (k, -k) pair: the first half of the azimuth
-  const int nphi = d.nphi, half = nphi / 2;
-  std::vector<int64_t> qs;
-  qs.reserve(p.M / 2);
-  for (int64_t q = 0; q < p.M; ++q)
-    if ((q % nphi) < half) qs.push_back(q);
-  p.Mh = (int64_t)qs.size();
-
-  // first taps (wrapped), kernel values and scales; processing order groups nodes by
-  // their first-tap tile (spatial locality of the interpolation reads)
-  std::vector<int> l0w(3 * p.Mh, 0);
-  std::vector<double> fr(3 * p.Mh, 0.0);
-  std::vector<int64_t> okey(p.Mh);
-  for (int64_t i = 0; i < p.Mh; ++i) {
-    const int64_t q = qs[i];
-    for (int a = 0; a < dim; ++a) {
-      const double k = p.quad.k[dim * q + a];
-      const int64_t l0 = fine_start(k, p.h[a], p.nf[a], W);
-      const double s = k * ((p.h[a] * (double)p.nf[a]) / (2.0 * M_PI));
-      fr[3 * i + a] = s - (double)l0;  // tap a sits at x = l0 + a - s
-      l0w[3 * i + a] = (int)(((l0 % p.nf[a]) + p.nf[a]) % p.nf[a]);
+// Spread work lists for the plan's current tile: per tile the visit list, the work units
+// (tile, owned plane) and the split units with their partial planes, uploaded to the
+// device, and the spread's launch geometry.  Replaces the lists of an earlier tile (the
+// spread-tile autotuner rebuilds them per candidate).
+int build_spread(Plan& p, cudaStream_t stream) {
+  const ddi_plan_desc& d = p.desc;
+  const int dim = p.dim, W = p.w;
+  const size_t rs = p.real_size(), cs = p.cx_size();
+  const size_t warp_bytes = spread_warp_bytes(p.spread_plane_cells() * cs, 2 * 32 * W * rs + 32 * (cs + 8));
+  if (warp_bytes * (kSpreadThreads / 32) > 200 * 1024) {
+    set_error("spread plane needs %zu bytes of shared memory per warp; choose a smaller tile", warp_bytes);
+    return DDI_ERR_ARG;
+  }
+  // the previous lists may still be read by queued work on this stream
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  for (void** q : {(void**)&p.d_visits, (void**)&p.d_units, (void**)&p.d_split, &p.d_partial})
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
     }
-    const int bx = l0w[3 * i] / p.tile[0], by = l0w[3 * i + 1] / p.tile[1], bz = l0w[3 * i + 2] / p.tile[2];
-    const int64_t bin = ((int64_t)bz * p.ntile[1] + by) * p.ntile[0] + bx;
-    const int64_t key = ((int64_t)l0w[3 * i + 2] * p.nf[1] + l0w[3 * i + 1]) * p.nf[0] + l0w[3 * i];
-    okey[i] = bin * p.fine_points() + key;
-  }
-  std::vector<int64_t> perm(p.Mh);
-  std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return okey[a] < okey[b]; });
-
-  p.order.resize(p.Mh);
-  std::vector<ushort4> l0s(p.Mh);
-  std::vector<double> psi((size_t)p.Mh * 3 * W, 1.0), scale(p.Mh);
-  const double hw = 0.5 * (double)W;
-  for (int64_t i = 0; i < p.Mh; ++i) {
-    const int64_t o = perm[i];
-    p.order[i] = qs[o];
-    l0s[i] = make_ushort4((unsigned short)l0w[3 * o], (unsigned short)l0w[3 * o + 1],
-                          (unsigned short)l0w[3 * o + 2], 0);
-    for (int a = 0; a < 3; ++a)
-      for (int t = 0; t < W; ++t) {
-        double v = a < dim ? 0.0 : (t == 0 ? 1.0 : 0.0);
-        if (a < dim) {
-          const double z = ((double)t - fr[3 * o + a]) / hw;
-          if (z * z < 1.0) v = std::exp(p.beta * (std::sqrt((1.0 - z) * (1.0 + z)) - 1.0));
-        }
-        psi[((size_t)i * 3 + a) * W + t] = v;
-      }
-    scale[i] = 2.0 * p.dv * p.quad.W[qs[o]];
-  }
+  p.bytes -= p.spread_bytes;
+  const size_t before = p.bytes;
 
   // spread visit lists: per tile, the nodes whose taps reach it with their starts relative
   // to the tile, ordered by (o_owned, o_row, ox) so that each owned plane's nodes are one
@@ -193,7 +142,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   const int ntiles = p.ntile[0] * p.ntile[1] * p.ntile[2];
   std::vector<std::vector<std::pair<int64_t, int4>>> lists(ntiles);
   for (int64_t i = 0; i < p.Mh; ++i) {
-    const int lv[3] = {l0s[i].x, l0s[i].y, l0s[i].z};
+    const int lv[3] = {p.h_l0[i].x, p.h_l0[i].y, p.h_l0[i].z};
     int ta[3][2], nt[3];
     for (int a = 0; a < 3; ++a) {
       const int l = a < dim ? lv[a] : 0;
@@ -282,6 +231,97 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   p.nsplit = (int)split.size();
   p.nslots = slot;
 
+  DDI_TRY(upload(p, (void**)&p.d_visits, visits, "visit lists", stream));
+  DDI_TRY(upload(p, (void**)&p.d_units, work, "work units", stream));
+  DDI_TRY(upload(p, (void**)&p.d_split, split, "split units", stream));
+  const size_t plane_cells = dim == 3 ? (size_t)p.tile[0] * p.tile[1] : (size_t)p.tile[0];
+  DDI_TRY(dev_alloc(p, &p.d_partial, cs * plane_cells * std::max(1, p.nslots), "partial planes"));
+  p.spread_bytes = p.bytes - before;
+  // the host vectors above die with this frame
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  return configure_kernels(p);
+}
+
+int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool gpe) {
+  std::string err;
+  {
+    const int st = normalise_desc(desc_in, &p.desc, &err);
+    if (st != DDI_OK) {
+      set_error("%s", err.c_str());
+      return st;
+    }
+  }
+  const ddi_plan_desc& d = p.desc;
+  DDI_CUDA(cudaGetDevice(&p.device));
+  p.dim = d.dim;
+  p.prec = d.precision;
+  p.dv = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    p.n[a] = a < d.dim ? d.n[a] : 1;
+    p.nf[a] = a < d.dim ? 2 * d.n[a] : 1;
+    p.h[a] = a < d.dim ? d.len[a] / (double)d.n[a] : 1.0;
+    if (a < d.dim) p.dv *= p.h[a];
+  }
+  p.w = kernel_width(d);
+  p.beta = kernel_beta(p.w);
+  build_quadrature(d, &p.quad);
+  p.M = p.quad.M;
+  choose_tile(p);
+  const int dim = d.dim, W = p.w;
+
+  // one node of each (k, -k) pair: the first half of the azimuth
+  const int nphi = d.nphi, half = nphi / 2;
+  std::vector<int64_t> qs;
+  qs.reserve(p.M / 2);
+  for (int64_t q = 0; q < p.M; ++q)
+    if ((q % nphi) < half) qs.push_back(q);
+  p.Mh = (int64_t)qs.size();
+
+  // first taps (wrapped), kernel values and scales; processing order groups nodes by
+  // their first-tap tile (spatial locality of the interpolation reads)
+  std::vector<int> l0w(3 * p.Mh, 0);
+  std::vector<double> fr(3 * p.Mh, 0.0);
+  std::vector<int64_t> okey(p.Mh);
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int64_t q = qs[i];
+    for (int a = 0; a < dim; ++a) {
+      const double k = p.quad.k[dim * q + a];
+      const int64_t l0 = fine_start(k, p.h[a], p.nf[a], W);
+      const double s = k * ((p.h[a] * (double)p.nf[a]) / (2.0 * M_PI));
+      fr[3 * i + a] = s - (double)l0;  // tap a sits at x = l0 + a - s
+      l0w[3 * i + a] = (int)(((l0 % p.nf[a]) + p.nf[a]) % p.nf[a]);
+    }
+    const int bx = l0w[3 * i] / p.tile[0], by = l0w[3 * i + 1] / p.tile[1], bz = l0w[3 * i + 2] / p.tile[2];
+    const int64_t bin = ((int64_t)bz * p.ntile[1] + by) * p.ntile[0] + bx;
+    const int64_t key = ((int64_t)l0w[3 * i + 2] * p.nf[1] + l0w[3 * i + 1]) * p.nf[0] + l0w[3 * i];
+    okey[i] = bin * p.fine_points() + key;
+  }
+  std::vector<int64_t> perm(p.Mh);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return okey[a] < okey[b]; });
+
+  p.order.resize(p.Mh);
+  std::vector<ushort4>& l0s = p.h_l0;
+  l0s.assign(p.Mh, ushort4{});
+  std::vector<double> psi((size_t)p.Mh * 3 * W, 1.0), scale(p.Mh);
+  const double hw = 0.5 * (double)W;
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    const int64_t o = perm[i];
+    p.order[i] = qs[o];
+    l0s[i] = make_ushort4((unsigned short)l0w[3 * o], (unsigned short)l0w[3 * o + 1],
+                          (unsigned short)l0w[3 * o + 2], 0);
+    for (int a = 0; a < 3; ++a)
+      for (int t = 0; t < W; ++t) {
+        double v = a < dim ? 0.0 : (t == 0 ? 1.0 : 0.0);
+        if (a < dim) {
+          const double z = ((double)t - fr[3 * o + a]) / hw;
+          if (z * z < 1.0) v = std::exp(p.beta * (std::sqrt((1.0 - z) * (1.0 + z)) - 1.0));
+        }
+        psi[((size_t)i * 3 + a) * W + t] = v;
+      }
+    scale[i] = 2.0 * p.dv * p.quad.W[qs[o]];
+  }
+
   // deconvolution factors 1/psihat(2 pi j'/nf), j' = j - n/2
   std::vector<double> dc;
   for (int a = 0; a < 3; ++a)
@@ -296,15 +336,18 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   DDI_TRY(upload_real(p, &p.d_psi, psi, "kernel values", stream, &k1));
   DDI_TRY(upload_real(p, &p.d_scale, scale, "node scales", stream, &k2));
   DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
-  DDI_TRY(upload(p, (void**)&p.d_visits, visits, "visit lists", stream));
-  DDI_TRY(upload(p, (void**)&p.d_units, work, "work units", stream));
-  DDI_TRY(upload(p, (void**)&p.d_split, split, "split units", stream));
   DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
   DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
   DDI_TRY(dev_alloc(p, &p.d_cz, cs * p.Mh * W, "node plane factors"));
   DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
-  const size_t plane_cells = dim == 3 ? (size_t)p.tile[0] * p.tile[1] : (size_t)p.tile[0];
-  DDI_TRY(dev_alloc(p, &p.d_partial, cs * plane_cells * std::max(1, p.nslots), "partial planes"));
+  for (int a = 0; a < 3; ++a) {
+    if (p.nf[a] > 1) DDI_TRY(make_twiddles(p, p.nf[a]));
+    if (p.n[a] > 1) DDI_TRY(make_twiddles(p, p.n[a]));
+  }
+  // the host vectors above die with this frame: finish the uploads first
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  DDI_TRY(build_spread(p, stream));
+  if (!gpe) return DDI_OK;
   const size_t N = (size_t)p.grid_points();
   DDI_TRY(dev_alloc(p, &p.d_psi1, cs * N, "gpe psi1"));
   DDI_TRY(dev_alloc(p, &p.d_rho, rs * N, "gpe rho"));
@@ -321,18 +364,32 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream) {
   }
   DDI_TRY(dev_alloc(p, &p.d_io_in, rs * N, "host io in"));
   DDI_TRY(dev_alloc(p, &p.d_io_out, rs * N, "host io out"));
-  for (int a = 0; a < 3; ++a) {
-    if (p.nf[a] > 1) DDI_TRY(make_twiddles(p, p.nf[a]));
-    if (p.n[a] > 1) DDI_TRY(make_twiddles(p, p.n[a]));
-  }
-  // the host vectors above die with this frame: finish the uploads first
-  DDI_CUDA(cudaStreamSynchronize(stream));
-  const size_t warp_bytes = spread_warp_bytes(p.spread_plane_cells() * cs, 2 * 32 * W * rs + 32 * (cs + 8));
-  if (warp_bytes * (kSpreadThreads / 32) > 200 * 1024) {
-    set_error("spread plane needs %zu bytes of shared memory per warp; choose a smaller tile", warp_bytes);
-    return DDI_ERR_ARG;
-  }
+  p.gpe_ready = true;
   return DDI_OK;
+}
+
+void fill_info(const Plan& p, ddi_plan_info* info) {
+  std::memset(info, 0, sizeof *info);
+  info->dim = p.dim;
+  info->precision = p.prec;
+  for (int a = 0; a < 3; ++a) {
+    info->n[a] = p.n[a];
+    info->nf[a] = p.nf[a];
+    info->tile[a] = p.tile[a];
+  }
+  info->width = p.w;
+  info->beta = p.beta;
+  info->nodes = p.M;
+  info->nodes_used = p.Mh;
+  info->spread_items = p.nunits;
+  info->spread_split_tiles = p.nsplit;
+  info->interp_items = (int)((p.Mh + 255) / 256);
+  info->kmax = p.desc.kmax;
+  info->nr = p.desc.nr;
+  info->ntheta = p.desc.ntheta;
+  info->nphi = p.desc.nphi;
+  info->device_bytes = p.bytes;
+  info->spread_tuned_ms = p.tuned_ms;
 }
 
 void destroy_plan(Plan& p) { free_plan(p); }
@@ -397,6 +454,7 @@ int ddi_plan_create(ddi_plan* out, const ddi_plan_desc* desc, void* stream) {
     return DDI_ERR_OOM;
   }
   int s = ddi::create_plan(h->p, desc, static_cast<cudaStream_t>(stream));
+  if (s == DDI_OK && desc->tile[0] < 0) s = ddi::tune_spread_tile(h->p, static_cast<cudaStream_t>(stream));
   if (s != DDI_OK) {
     ddi::destroy_plan(h->p);
     delete h;
@@ -418,26 +476,7 @@ int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info) {
     ddi::set_error("plan and info must not be NULL");
     return DDI_ERR_ARG;
   }
-  const Plan& p = plan->p;
-  info->dim = p.dim;
-  info->precision = p.prec;
-  for (int a = 0; a < 3; ++a) {
-    info->n[a] = p.n[a];
-    info->nf[a] = p.nf[a];
-    info->tile[a] = p.tile[a];
-  }
-  info->width = p.w;
-  info->beta = p.beta;
-  info->nodes = p.M;
-  info->nodes_used = p.Mh;
-  info->spread_items = p.nunits;
-  info->spread_split_tiles = p.nsplit;
-  info->interp_items = (int)((p.Mh + 255) / 256);
-  info->kmax = p.desc.kmax;
-  info->nr = p.desc.nr;
-  info->ntheta = p.desc.ntheta;
-  info->nphi = p.desc.nphi;
-  info->device_bytes = p.bytes;
+  ddi::fill_info(plan->p, info);
   return DDI_OK;
 }
 

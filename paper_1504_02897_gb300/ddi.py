@@ -44,7 +44,8 @@ class PlanInfo(ctypes.Structure):
                 ("nodes", ctypes.c_int64), ("nodes_used", ctypes.c_int64), ("tile", ctypes.c_int * 3),
                 ("spread_items", ctypes.c_int), ("spread_split_tiles", ctypes.c_int),
                 ("interp_items", ctypes.c_int), ("kmax", ctypes.c_double), ("nr", ctypes.c_int),
-                ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+                ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
+                ("spread_tuned_ms", ctypes.c_double)]
 
 
 class GpeStats(ctypes.Structure):
@@ -59,7 +60,12 @@ class GpeStats(ctypes.Structure):
 
 EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_plan_create", "ddi_plan_destroy",
            "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
-           "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc"]
+           "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc",
+           "ddi_batch_create", "ddi_batch_destroy", "ddi_batch_size", "ddi_batch_get_info", "ddi_batch_apply",
+           "ddi_batch_graph_stats"]
+
+BATCH_GRAPH = 1
+BATCH_AUTOTUNE = 2
 
 _lib = None
 
@@ -97,6 +103,12 @@ def load():
         "gpe_ground_state": ([vp, vp, vp, cd, cd, cd, cd, ci, cd, ci, ci, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_step_adjoint": ([vp, vp, vp, vp, vp, cd, cd, cd, vp], ci),
         "gpe_sums_noalloc": ([vp, vp, ctypes.c_int64, ci, vp, vp], ci),
+        "ddi_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(PlanDesc), ci, ci, vp], ci),
+        "ddi_batch_destroy": ([vp], ci),
+        "ddi_batch_size": ([vp], ci),
+        "ddi_batch_get_info": ([vp, ci, ctypes.POINTER(PlanInfo)], ci),
+        "ddi_batch_apply": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], ci),
+        "ddi_batch_graph_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -277,6 +289,66 @@ class Plan:
                                        self._req(V), float(beta), float(lam), float(dt),
                                        ctypes.c_void_p(_stream(stream))), "gpe_step_adjoint")
         return cot
+
+
+class Batch:
+    """Many DDI evaluations in one call (ddi_batch_*): one plan per descriptor, items run
+    concurrently on side streams, optionally replayed from a recorded CUDA graph, spread
+    tiles optionally picked by the autotuner."""
+
+    def __init__(self, descs, graph=True, autotune=True, stream=None):
+        import torch
+        lib = load()
+        self.descs = list(descs)
+        arr = (PlanDesc * len(self.descs))(*self.descs)
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+        h = ctypes.c_void_p()
+        _check(lib.ddi_batch_create(ctypes.byref(h), arr, len(self.descs), flags, ctypes.c_void_p(_stream(stream))),
+               "ddi_batch_create")
+        self._h = h
+        self.infos = []
+        for i in range(len(self.descs)):
+            info = PlanInfo()
+            _check(lib.ddi_batch_get_info(self._h, i, ctypes.byref(info)), "ddi_batch_get_info")
+            self.infos.append(info)
+        self.shapes = [tuple(reversed([d.n[a] for a in range(d.dim)])) for d in self.descs]
+        self.dtypes = [torch.float64 if d.precision == FP64 else torch.float32 for d in self.descs]
+
+    def __len__(self):
+        return len(self.descs)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ddi_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, rhos, outs=None, stream=None):
+        import torch
+        if len(rhos) != len(self):
+            raise ValueError(f"expected {len(self)} densities, got {len(rhos)}")
+        if outs is None:
+            outs = [torch.empty_like(r) for r in rhos]
+        for i, (r, o) in enumerate(zip(rhos, outs)):
+            for t in (r, o):
+                if (not t.is_cuda or t.dtype != self.dtypes[i] or not t.is_contiguous()
+                        or tuple(t.shape) != self.shapes[i]):
+                    raise ValueError(f"item {i}: expected a contiguous CUDA tensor of dtype {self.dtypes[i]} and "
+                                     f"shape {self.shapes[i]}, got {t.dtype} {tuple(t.shape)} on {t.device}")
+        rp = (ctypes.c_void_p * len(self))(*[r.data_ptr() for r in rhos])
+        op = (ctypes.c_void_p * len(self))(*[o.data_ptr() for o in outs])
+        _check(load().ddi_batch_apply(self._h, rp, op, ctypes.c_void_p(_stream(stream))), "ddi_batch_apply")
+        return outs
+
+    def graph_stats(self):
+        rec, lau = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        _check(load().ddi_batch_graph_stats(self._h, ctypes.byref(rec), ctypes.byref(lau)), "ddi_batch_graph_stats")
+        return rec.value, lau.value
 
 
 def sums_noalloc(psi, V, sums, stream=None):

@@ -1,0 +1,233 @@
+"""GPU batches of DDI evaluations (ddi_batch_*) and the spread-tile autotuner, through
+the C ABI, against the FP64 oracle and against single-plan ddi_apply.
+
+Tolerances as for single plans (relative L-infinity, normalised by max |oracle|):
+1e-12 for FP64 items, 1e-6 for FP32 items."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nudft
+from oracle import quadrature as qd
+from paper_1504_02897_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-6}
+
+
+def fp32_floor(it, ref):
+    """Relative change of the exact sum when the density is rounded to FP32 (the FP32
+    path's input), by the oracle.  In 2D the weights grow like |k| up to R = pi/h, so
+    this alone is 3e-7 .. 1.2e-6 of max|Phi| for the 128^2 batched densities and grows
+    with N; the FP32 path (input/deconvolution, forward FFT and interpolation, spread and
+    inverse FFT, each rounding at that level) is held to 8x it when that exceeds 1e-6."""
+    t = qd.plan_tables(len(it["n"]), it["n"], it["len"], it["axis"])
+    r32 = nudft.ddi(it["rho"].astype(np.float32).astype(np.float64), t, it["n"], it["lo"], it["len"])
+    return _relinf(r32, ref)
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    ddi.load()
+    torch.cuda.init()
+    return ddi
+
+
+def _relinf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _desc(D, it, precision, tile=None):
+    dim = len(it["n"])
+    return D.make_desc(dim, it["n"], it["lo"], it["len"], it["axis"], precision=precision, tile=tile)
+
+
+def _oracle(it):
+    dim = len(it["n"])
+    t = qd.plan_tables(dim, it["n"], it["len"], it["axis"])
+    return nudft.ddi(it["rho"], t, it["n"], it["lo"], it["len"])
+
+
+def _tensors(items, descs):
+    import torch
+    out = []
+    for it, d in zip(items, descs):
+        dt = torch.float64 if d.precision == 0 else torch.float32
+        out.append(torch.from_numpy(np.ascontiguousarray(it["rho"])).to("cuda", dt))
+    return out
+
+
+def _mixed_items():
+    # 2D densities shaped like the batched workload (random box, tilt, 4 Gaussians) at
+    # small sizes, plus two 3D mixtures
+    items = synth.batch_2d(count=6, seed=3, sizes=(32, 48, 64, 96))
+    for seed, (N, L) in enumerate([(24, 6.0), (32, 8.0)]):
+        it = synth.gaussian_mixture_density(N, L, seed=seed, centre=L / 3)
+        a = math.radians(20.0 + 25.0 * seed)
+        items.append(dict(it, axis=(math.sin(a), 0.0, math.cos(a))))
+    return items
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_mixed_matches_oracle(D, graph):
+    # mixed dims, sizes, axes and precisions in one batch, autotuned tiles
+    import torch
+    items = _mixed_items()
+    descs = [_desc(D, it, precision=i % 2) for i, it in enumerate(items)]
+    b = D.Batch(descs, graph=graph, autotune=True)
+    rhos = _tensors(items, descs)
+    outs = b.apply(rhos)
+    torch.cuda.synchronize()
+    for i, (it, d, o) in enumerate(zip(items, descs, outs)):
+        assert b.infos[i].spread_tuned_ms > 0.0
+        ref = _oracle(it)
+        err = _relinf(o.double().cpu().numpy(), ref)
+        tol = TOL[d.precision]
+        if d.precision == 1 and len(it["n"]) == 2:
+            tol = max(tol, 8.0 * fp32_floor(it, ref))
+        assert err <= tol, (i, it["n"], d.precision, err)
+    b.close()
+
+
+def test_batch_bitwise_equals_single_plans(D):
+    # same tiles (built-in choice, no autotuning): the batch runs the same kernels with
+    # the same work lists as ddi_apply, so every item is bit-identical
+    import torch
+    items = _mixed_items()
+    descs = [_desc(D, it, precision=(i + 1) % 2) for i, it in enumerate(items)]
+    b = D.Batch(descs, graph=True, autotune=False)
+    rhos = _tensors(items, descs)
+    outs = b.apply(rhos)
+    torch.cuda.synchronize()
+    for i, (it, d) in enumerate(zip(items, descs)):
+        dim = len(it["n"])
+        p = D.Plan(dim, it["n"], it["lo"], it["len"], it["axis"], precision=d.precision)
+        assert tuple(p.info.tile) == tuple(b.infos[i].tile)
+        ref = p.apply(rhos[i])
+        torch.cuda.synchronize()
+        assert torch.equal(ref, outs[i]), i
+        p.close()
+    b.close()
+
+
+def test_batch_graph_replay_and_new_pointers(D):
+    import torch
+    items = synth.batch_2d(count=5, seed=7, sizes=(32, 64, 128))
+    descs = [_desc(D, it, precision=1) for it in items]
+    b = D.Batch(descs, graph=True, autotune=True)
+    rhos = _tensors(items, descs)
+    outs = [torch.empty_like(r) for r in rhos]
+    b.apply(rhos, outs)
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.zero_()
+    b.apply(rhos, outs)  # same pointers: replay
+    torch.cuda.synchronize()
+    assert b.graph_stats() == (1, 2)
+    for f, o in zip(first, outs):
+        assert torch.equal(f, o)
+    # new output buffers and an in-place item: the graph is recorded again
+    outs2 = [torch.empty_like(r) for r in rhos]
+    rin = rhos[2].clone()
+    outs2[2] = rin
+    rhos2 = list(rhos)
+    rhos2[2] = rin
+    b.apply(rhos2, outs2)
+    torch.cuda.synchronize()
+    assert b.graph_stats() == (2, 3)
+    for f, o in zip(first, outs2):
+        assert torch.equal(f, o)
+    # replays keep following the inputs' contents
+    rhos[0].mul_(2.0)
+    b.apply(rhos2, outs2)
+    torch.cuda.synchronize()
+    assert b.graph_stats() == (2, 4)
+    assert _relinf(outs2[0].double().cpu().numpy(), 2.0 * first[0].double().cpu().numpy()) <= 1e-6
+    b.close()
+
+
+def test_batch_rejects_bad_input(D):
+    import torch
+    items = synth.batch_2d(count=2, seed=1, sizes=(32,))
+    descs = [_desc(D, it, precision=1) for it in items]
+    bad = D.make_desc(2, (30, 32), (-4.0, -4.0), (8.0, 8.0), (1.0, 0.0, 0.0), precision=1)
+    with pytest.raises(D.DDIError) as e:
+        D.Batch(descs + [bad])
+    assert "item 2" in str(e.value)
+    b = D.Batch(descs, graph=False, autotune=False)
+    rhos = _tensors(items, descs)
+    with pytest.raises(ValueError):
+        b.apply(rhos[:1])
+    with pytest.raises(ValueError):
+        b.apply([rhos[0], rhos[1].double()])
+    b.close()
+
+
+def test_autotuned_plan_and_cache(D):
+    # tile[0] < 0: the plan's spread tile is picked by timing candidates; a second plan of
+    # the same node-set shape (other box length and axis) reuses the cached choice
+    import torch
+    N, L = 48, 9.0
+    it = synth.gaussian_mixture_density(N, L, seed=4, centre=3.0)
+    n, lo, ln, rho = it["n"], it["lo"], it["len"], it["rho"]
+    p1 = D.Plan(3, n, lo, ln, (0.0, 0.6, 0.8), precision=1, tile=(-1, 0, 0))
+    assert p1.info.spread_tuned_ms > 0.0
+    got = p1.apply(torch.from_numpy(rho).to("cuda", torch.float32))
+    torch.cuda.synchronize()
+    t = qd.plan_tables(3, n, ln, (0.0, 0.6, 0.8))
+    assert _relinf(got.double().cpu().numpy(), nudft.ddi(rho, t, n, lo, ln)) <= TOL[1]
+    n2, lo2, ln2 = synth.box(N, 11.0, 3)
+    p2 = D.Plan(3, n2, lo2, ln2, (1.0, 0.0, 0.0), precision=1, tile=(-1, 0, 0))
+    assert tuple(p2.info.tile) == tuple(p1.info.tile)
+    assert p2.info.spread_tuned_ms == p1.info.spread_tuned_ms
+    p1.close()
+    p2.close()
+
+
+def test_batch_2d_1024_trace_identity(D):
+    # 2D trace identity at the largest batched size: with m = n, the symbol summed over
+    # n = e_x, e_y, e_z is 3/2 [(k_x^2 + k_y^2)/|k| - |k|] = 0 at every node, so the three
+    # potentials of one density sum to zero up to the NUFFT error
+    import torch
+    it = synth.batch_2d(count=1, seed=11, sizes=(1024,))[0]
+    items = [dict(it, axis=a) for a in ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))]
+    descs = [_desc(D, x, precision=1) for x in items]
+    b = D.Batch(descs, graph=True, autotune=True)
+    outs = b.apply(_tensors(items, descs))
+    torch.cuda.synchronize()
+    s = (outs[0].double() + outs[1].double() + outs[2].double()).abs().max().item()
+    scale = max(o.double().abs().max().item() for o in outs)
+    assert s / scale <= 2e-6
+    b.close()
+
+
+def test_batch_96_densities_2d(D):
+    # the batched 2D workload: 96 densities, N in {128, 256, 512, 1024}, box length
+    # U[8, 16], tilt U[0, 90] degrees, 4 Gaussians each, quadrature 2N x 2N, FP32,
+    # autotuned tiles, one recorded graph.  Oracle parity on a subset (every size the
+    # oracle finishes in seconds: four 128^2 items and one 256^2 item), to 1e-6 or 8x
+    # the item's FP32 input-rounding floor, whichever is larger.
+    import torch
+    items = synth.batch_2d(count=96, seed=0)
+    descs = [_desc(D, it, precision=1) for it in items]
+    b = D.Batch(descs, graph=True, autotune=True)
+    rhos = _tensors(items, descs)
+    outs = b.apply(rhos)
+    torch.cuda.synchronize()
+    assert b.graph_stats() == (1, 1)
+    for o in outs:
+        assert bool(torch.isfinite(o).all())
+    small = [i for i, it in enumerate(items) if it["n"][0] == 128][:4]
+    small += [i for i, it in enumerate(items) if it["n"][0] == 256][:1]
+    for i in small:
+        ref = _oracle(items[i])
+        err = _relinf(outs[i].double().cpu().numpy(), ref)
+        floor = fp32_floor(items[i], ref)
+        assert err <= max(TOL[1], 8.0 * floor), (i, items[i]["n"], err, floor)
+    b.close()

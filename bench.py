@@ -234,7 +234,8 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
 
     w = synth.gaussian_mixture_density(N, L, seed=rank)
-    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP32, **SIZES)
+    # spread tile picked by the autotuner (timed on this device, cached per shape)
+    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP32, tile=(-1, 0, 0), **SIZES)
     rho = torch.from_numpy(w["rho"]).to(dev, torch.float32)
     phi = torch.empty_like(rho)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -358,7 +359,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _workload_cfg({"fp32_rel_err_vs_fp64": err32, "fp64_ddi_per_s": 1e3 / (sum(t64) / len(t64)),
                                      "nufft_points_per_s": value * 2 * N * 64 * 128,
-                                     "kernel_width": info.width, "wall_s": wall}),
+                                     "kernel_width": info.width, "spread_tile": list(info.tile),
+                                     "wall_s": wall}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dominant,
                          "kernel_ms": avg[dominant], "peak_source": src + " hbm_gbs (copy)"},

@@ -51,10 +51,10 @@ namespace {
 std::vector<std::array<int, 3>> tile_candidates(const Plan& p) {
   if (p.dim == 3) {
     if (p.prec == DDI_FP32)
-      return {{32, 16, 16}, {32, 32, 8}, {16, 16, 16}, {64, 16, 8}, {32, 16, 8}, {32, 8, 16}, {16, 16, 32}};
+      return {{32, 16, 16}, {32, 32, 8}, {16, 16, 16}, {64, 16, 8}, {64, 16, 16}, {32, 16, 8}, {32, 8, 16}, {16, 16, 32}};
     return {{16, 16, 16}, {32, 16, 16}, {16, 16, 32}, {32, 32, 16}};
   }
-  return {{64, 64, 1}, {128, 32, 1}, {32, 32, 1}, {64, 32, 1}, {128, 64, 1}, {256, 16, 1}, {32, 64, 1}, {64, 128, 1}};
+  return {{32, 16, 1}, {32, 32, 1}, {64, 16, 1}, {16, 16, 1}, {64, 32, 1}, {32, 8, 1}, {128, 16, 1}};
 }
 
 }  // namespace

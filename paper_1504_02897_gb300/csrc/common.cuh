@@ -66,7 +66,7 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.
 // ---- spread work list ------------------------------------------------------------
 struct SpreadUnit {
   int tile;   // linear tile index (tz * ntiles_y + ty) * ntiles_x + tx
-  int plane;  // owned plane of the tile (z in 3D, y row in 2D)
+  int plane;  // owned z-plane of the tile in 3D; 0 in 2D (the unit is the whole tile)
   int lo, hi; // range of visit-list entries whose taps cover the plane
   int slot;   // -1: write the plane to the fine grid; >= 0: write to partial slot
 };
@@ -92,17 +92,11 @@ __host__ __device__ inline int rel_start(int l0, int T0, int nf, int w) {
   if (o > nf - w) o -= nf;
   return o;
 }
-// Row stride (cells) of the spread's shared-memory tile.  A half-warp touches two 8-cell
-// row segments; they must fall in different halves of the 128-byte bank window.  Rows of
-// a multiple of 16 cells are unpadded and swizzled (x ^ 8 on odd rows); other widths are
-// padded to a stride = 8 (mod 16).
-__host__ __device__ inline bool spread_swizzle(int TX) { return TX % 16 == 0; }
-__host__ __device__ inline int spread_row_stride(int TX) {
-  return spread_swizzle(TX) ? TX : TX + ((8 - TX % 16) + 16) % 16;
-}
-__host__ __device__ inline int spread_cell(int y, int x, int RS, bool swz) {
-  return y * RS + (swz ? (x ^ ((y & 1) << 3)) : x);
-}
+// Row stride (cells) of the spread's shared-memory plane.  A warp touches 4 rows of 8
+// consecutive cells (8-byte cells: half the 128-byte bank window each); with a stride of
+// 8 (mod 16) cells consecutive rows fall in opposite halves, so the 32 accesses take the
+// minimum two wavefronts.  (16-byte cells fill the window with one 8-cell row segment.)
+__host__ __device__ inline int spread_row_stride(int TX) { return TX + ((8 - TX % 16) + 16) % 16; }
 
 // ---- the plan ----------------------------------------------------------------------
 struct Plan {
@@ -133,7 +127,6 @@ struct Plan {
   void* d_psi = nullptr;      // T [Mh][3][w]: kernel values along x, y, z at the w taps
   void* d_scale = nullptr;    // T [Mh]: 2 h^d W_q
   void* d_c = nullptr;        // cx [Mh]: node values c_q
-  void* d_cz = nullptr;       // cx [Mh][w]: c_q times the kernel along the spread's owned axis
   void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
   void* d_partial = nullptr;  // cx [nslots * tile cells]
@@ -143,7 +136,7 @@ struct Plan {
   int* d_counter = nullptr;   // unit counter of the persistent spread
   long long visits = 0;       // total visit-list entries
   long long pairs = 0;        // total (node, plane) pairs of all units
-  int npl = 1;                // owned planes per tile (z-planes in 3D, y-rows in 2D)
+  int npl = 1;                // owned planes per tile (z-planes in 3D; 1 in 2D)
   int nunits = 0;
   size_t spread_smem = 0;     // launch geometry of the spread (fixed per plan)
   int spread_blocks = 1;
@@ -178,10 +171,7 @@ struct Plan {
 
   int64_t grid_points() const { return (int64_t)n[0] * n[1] * n[2]; }
   // cells of one owned plane's shared-memory buffer (padded row stride)
-  size_t spread_plane_cells() const {
-    const size_t rs = (size_t)spread_row_stride(tile[0]);
-    return dim == 3 ? (size_t)tile[1] * rs : rs;
-  }
+  size_t spread_plane_cells() const { return (size_t)tile[1] * spread_row_stride(tile[0]); }
   int64_t fine_points() const { return (int64_t)nf[0] * nf[1] * nf[2]; }
   size_t real_size() const { return prec == DDI_FP64 ? 8 : 4; }
   size_t cx_size() const { return prec == DDI_FP64 ? 16 : 8; }
@@ -207,9 +197,18 @@ template <typename T> int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t 
 template <typename T> int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s);        // U (fine grid) -> phi
 
 // ---- NUFFT stages (nufft.cu) --------------------------------------------------------
-template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);         // rho -> d_c, d_cz
+template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);         // rho -> d_c
 template <typename T> int run_type1_from_c(Plan& p, T* phi, cudaStream_t s);       // d_c -> phi
 template <typename T> int run_ddi(Plan& p, const T* rho, T* phi, cudaStream_t s);
+// bytes of the spread's per-warp node stage of 32 nodes: psi_x and psi_y rows (psi_y padded
+// to the lanes' row groups) and a 16-byte (FP32) / 32-byte (FP64) header per node
+__host__ __device__ constexpr int spread_rows_per_instr(int w) { return 32 / (w <= 8 ? 8 : 16); }
+__host__ __device__ constexpr size_t spread_stage_bytes(int w, size_t real_bytes) {
+  return 32 * (size_t)w * real_bytes +
+         32 * (size_t)(((w + spread_rows_per_instr(w) - 1) / spread_rows_per_instr(w)) * spread_rows_per_instr(w)) *
+             real_bytes +
+         32 * (real_bytes == 4 ? 16 : 32);
+}
 // shared memory of one spread warp: its plane buffer and its node stage, 16-byte aligned
 __host__ __device__ inline size_t spread_warp_bytes(size_t plane_bytes, size_t stage_bytes) {
   return ((plane_bytes + 15) & ~(size_t)15) + ((stage_bytes + 15) & ~(size_t)15);

@@ -13,10 +13,12 @@ struct PlainLines {
   using C = cx_t<T>;
   C* data;
   LineGeom g;
+  using Ref = long long;  // offset of the line's first element
   __host__ __device__ long long nlines() const { return g.nlines; }
   __device__ bool contig() const { return g.se == 1; }
-  __device__ C load(long long L, int i) const { return data[line_off(g, L) + (long long)i * g.se]; }
-  __device__ void store(long long L, int i, C v) const { data[line_off(g, L) + (long long)i * g.se] = v; }
+  __device__ Ref ref(long long L) const { return line_off(g, L); }
+  __device__ C load(Ref r, int i) const { return __ldg(data + r + (long long)i * g.se); }
+  __device__ void store(Ref r, int i, C v) const { data[r + (long long)i * g.se] = v; }
 };
 
 }  // namespace

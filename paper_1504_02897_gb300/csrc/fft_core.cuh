@@ -175,43 +175,68 @@ __device__ __forceinline__ long long line_off(const LineGeom& g, long long L) {
 }
 
 // Generic batched-line FFT: a policy P supplies nlines(), contig() (element index fastest
-// in memory), load(L, i) and store(L, i, v) for element i of line L.
+// in memory), ref(L) (the line's addresses, computed once per line by one thread) and
+// load(ref, i) / store(ref, i, v) for element i of the line.
 template <typename T, int N, int LPB, int DIR, typename P>
 __global__ void __launch_bounds__(LPB * Shape<N>::TPL)
     k_fft_policy(P pol, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
+  using Ref = typename P::Ref;
   constexpr int LS = Shape<N>::LS;
   constexpr int TPL = Shape<N>::TPL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Ref refs[LPB];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const long long L0 = (long long)blockIdx.x * LPB;
-  const long long nl = pol.nlines();
-  if (pol.contig()) {
-    for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-      const int b = idx / N, i = idx % N;
-      const long long L = L0 + b;
-      if (L < nl) sm[b * LS + pidx(i)] = pol.load(L, i);
+  const long long left = pol.nlines() - L0;
+  const int nb = left < LPB ? (int)left : LPB;  // lines of this CTA
+  if ((int)threadIdx.x < nb) refs[threadIdx.x] = pol.ref(L0 + threadIdx.x);
+  __syncthreads();
+  // each thread moves EPT elements; all its global loads are issued before any shared
+  // store (and all its shared loads before any global store) so that they overlap
+  constexpr int NT = LPB * TPL;
+  constexpr int EPT = LPB * N / NT;
+  const bool contig = pol.contig();
+  auto coord = [&](int k, int& b, int& i) {
+    const int idx = (int)threadIdx.x + k * NT;
+    if (contig) {
+      b = idx / N;
+      i = idx % N;
+    } else {
+      i = idx / LPB;
+      b = idx % LPB;
     }
-  } else {
-    for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-      const int i = idx / LPB, b = idx % LPB;
-      const long long L = L0 + b;
-      if (L < nl) sm[b * LS + pidx(i)] = pol.load(L, i);
+  };
+  {
+    C v[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      int b, i;
+      coord(k, b, i);
+      v[k] = b < nb ? pol.load(refs[b], i) : cmk<C>((T)0, (T)0);
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      int b, i;
+      coord(k, b, i);
+      sm[b * LS + pidx(i)] = v[k];
     }
   }
   __syncthreads();
   Stages<C, N, DIR, 1>::run(sm + (threadIdx.x / TPL) * LS, threadIdx.x % TPL, tw);
-  if (pol.contig()) {
-    for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-      const int b = idx / N, i = idx % N;
-      const long long L = L0 + b;
-      if (L < nl) pol.store(L, i, sm[b * LS + pidx(i)]);
+  {
+    C v[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      int b, i;
+      coord(k, b, i);
+      v[k] = sm[b * LS + pidx(i)];
     }
-  } else {
-    for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-      const int i = idx / LPB, b = idx % LPB;
-      const long long L = L0 + b;
-      if (L < nl) pol.store(L, i, sm[b * LS + pidx(i)]);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      int b, i;
+      coord(k, b, i);
+      if (b < nb) pol.store(refs[b], i, v[k]);
     }
   }
 }

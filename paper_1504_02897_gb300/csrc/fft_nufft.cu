@@ -11,7 +11,9 @@
 //            x: only the rows in the block; the x in the block are stored as
 //               Re(u) / psihat into phi (crop, deconvolution and real part fused).
 // Grid positions that are not read are never written in the same evaluation, so no
-// zero-fill of the fine grid is needed.
+// zero-fill of the fine grid is needed.  Each CTA reads its own lines before it writes
+// them and no other CTA touches them, so the in-place passes may load through the
+// read-only data cache.
 #include "fft_core.cuh"
 
 namespace ddi {
@@ -43,47 +45,50 @@ struct Geo {
 
 // forward x with the pad: lines = grid rows (jy, jz)
 template <typename T>
+struct RowRef {
+  long long grid;  // offset of the row in rho / phi
+  long long fine;  // offset of the row in the fine grid
+  T dy, dz;        // deconvolution factors of the row
+};
+
+template <typename T>
 struct PadX {
   using C = cx_t<T>;
+  using Ref = RowRef<T>;
   Geo<T> g;
   const T* rho;
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }
   __device__ bool contig() const { return true; }
-  __device__ C load(long long L, int i) const {
+  __device__ Ref ref(long long L) const {
+    const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
+    return Ref{L * g.ax.n, g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), 0), g.dcy[jy], g.dcz[jz]};
+  }
+  __device__ C load(const Ref& r, int i) const {
     if (!g.ax.in_block(i)) return cmk<C>((T)0, (T)0);
-    const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
     const int jx = g.ax.grid_of(i);
-    const T v = rho[((long long)jz * g.ay.n + jy) * g.ax.n + jx] * (g.dcx[jx] * g.dcy[jy] * g.dcz[jz]);
-    return cmk<C>(v, (T)0);
+    return cmk<C>(__ldg(rho + r.grid + jx) * (g.dcx[jx] * r.dy * r.dz), (T)0);
   }
-  __device__ void store(long long L, int i, C v) const {
-    const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
-    g.fine[g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), i)] = v;
-  }
+  __device__ void store(const Ref& r, int i, C v) const { g.fine[r.fine + i] = v; }
 };
 
 // y lines of the planes z in the block: forward (pruned input) or inverse (pruned output)
 template <typename T, bool FWD>
 struct BlockY {
   using C = cx_t<T>;
+  using Ref = long long;  // fine-grid offset of the line's first element
   Geo<T> g;
   __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.az.n; }
   __device__ bool contig() const { return false; }
-  __device__ void pos(long long L, int& lx, int& lz) const {
-    lx = (int)(L % g.ax.nf);
-    lz = g.az.fine_of((int)(L / g.ax.nf));
+  __device__ Ref ref(long long L) const {
+    return g.fidx(g.az.fine_of((int)(L / g.ax.nf)), 0, (int)(L % g.ax.nf));
   }
-  __device__ C load(long long L, int i) const {
+  __device__ C load(Ref r, int i) const {
     if (FWD && !g.ay.in_block(i)) return cmk<C>((T)0, (T)0);
-    int lx, lz;
-    pos(L, lx, lz);
-    return g.fine[g.fidx(lz, i, lx)];
+    return __ldg(g.fine + r + (long long)i * g.ax.nf);
   }
-  __device__ void store(long long L, int i, C v) const {
+  __device__ void store(Ref r, int i, C v) const {
     if (!FWD && !g.ay.in_block(i)) return;
-    int lx, lz;
-    pos(L, lx, lz);
-    g.fine[g.fidx(lz, i, lx)] = v;
+    g.fine[r + (long long)i * g.ax.nf] = v;
   }
 };
 
@@ -91,16 +96,18 @@ struct BlockY {
 template <typename T, bool FWD>
 struct AllZ {
   using C = cx_t<T>;
+  using Ref = long long;  // the column's (y, x) offset
   Geo<T> g;
   __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.ay.nf; }
   __device__ bool contig() const { return false; }
-  __device__ C load(long long L, int i) const {
+  __device__ Ref ref(long long L) const { return L; }
+  __device__ C load(Ref r, int i) const {
     if (FWD && !g.az.in_block(i)) return cmk<C>((T)0, (T)0);
-    return g.fine[(long long)i * g.ay.nf * g.ax.nf + L];
+    return __ldg(g.fine + (long long)i * g.ay.nf * g.ax.nf + r);
   }
-  __device__ void store(long long L, int i, C v) const {
+  __device__ void store(Ref r, int i, C v) const {
     if (!FWD && !g.az.in_block(i)) return;
-    g.fine[(long long)i * g.ay.nf * g.ax.nf + L] = v;
+    g.fine[(long long)i * g.ay.nf * g.ax.nf + r] = v;
   }
 };
 
@@ -108,19 +115,20 @@ struct AllZ {
 template <typename T>
 struct CropX {
   using C = cx_t<T>;
+  using Ref = RowRef<T>;
   Geo<T> g;
   T* phi;
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }
   __device__ bool contig() const { return true; }
-  __device__ C load(long long L, int i) const {
+  __device__ Ref ref(long long L) const {
     const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
-    return g.fine[g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), i)];
+    return Ref{L * g.ax.n, g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), 0), g.dcy[jy], g.dcz[jz]};
   }
-  __device__ void store(long long L, int i, C v) const {
+  __device__ C load(const Ref& r, int i) const { return __ldg(g.fine + r.fine + i); }
+  __device__ void store(const Ref& r, int i, C v) const {
     if (!g.ax.in_block(i)) return;
-    const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
     const int jx = g.ax.grid_of(i);
-    phi[((long long)jz * g.ay.n + jy) * g.ax.n + jx] = v.x * (g.dcx[jx] * g.dcy[jy] * g.dcz[jz]);
+    phi[r.grid + jx] = v.x * (g.dcx[jx] * r.dy * r.dz);
   }
 };
 

@@ -17,14 +17,15 @@
 //
 // Launches (fft_nufft.cu holds the FFT passes):
 //   forward FFT x (pad + deconvolution fused), y, z, pruned to the padded block
-//   k_interp    one thread per node: f_q = sum over the w^d taps of psi F; writes
-//               c_q = 2 h^d W_q f_q and c_q psi_z (the spread's per-plane factors)
-//   k_spread    owner-computes spread over work units (tile, z-plane): a warp takes a
-//               unit, streams the nodes whose taps reach that plane (ranges built by the
-//               plan) and adds c psi_z psi_y psi_x into its shared-memory plane with plain
-//               read-modify-writes (no other unit owns those cells); runs of nodes with
-//               the same footprint are summed in registers first.  Every plane is
-//               written once; long units are split into partial planes
+//   k_interp    8 (w <= 8) or 16 lanes per node: f_q = sum over the w^d taps of psi F,
+//               each footprint row read as one contiguous segment; writes
+//               c_q = 2 h^d W_q f_q
+//   k_spread    owner-computes spread over work units (tile, z-plane in 3D; tile in
+//               2D): a warp takes a unit, streams the nodes whose taps reach that plane
+//               (ranges built by the plan) and adds c psi_z psi_y psi_x into its
+//               shared-memory plane with plain read-modify-writes (no other unit owns
+//               those cells).  Every plane is written once; long units are split into
+//               partial planes
 //   k_reduce    sums the partial planes of split units
 //   inverse FFT z, y, x (pruned to the cropped block; x fused with crop, deconvolution
 //               and real part)
@@ -55,81 +56,100 @@ GridDims dims_of(const Plan& p) {
 // i in [0, 2 nf) -> i mod nf
 __device__ __forceinline__ int wrap1(int i, int nf) { return i >= nf ? i - nf : i; }
 
+// kernel values of one axis of a node (w contiguous values), in 16- or 8-byte loads
+template <typename T, int W>
+__device__ __forceinline__ void load_taps(const T* __restrict__ src, T (&dst)[W]) {
+  if constexpr (sizeof(T) == 4 && W % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < W / 4; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src) + k);
+      dst[4 * k] = v.x;
+      dst[4 * k + 1] = v.y;
+      dst[4 * k + 2] = v.z;
+      dst[4 * k + 3] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && W % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(src) + k);
+      dst[2 * k] = v.x;
+      dst[2 * k + 1] = v.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && W % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(src) + k);
+      dst[2 * k] = v.x;
+      dst[2 * k + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k) dst[k] = __ldg(src + k);
+  }
+}
+
 // ---- interpolation (type 2) -----------------------------------------------------------------
+// XL lanes per node (one x tap each; 8 for w <= 8, else 16), 32 / XL nodes per warp: the
+// lanes of a node read each footprint row of the fine grid as one contiguous segment,
+// accumulate the psi_y (and psi_z) weighted sums in registers, and the node's value is
+// the psi_x-weighted sum over its lanes (shuffle reduction).
 template <typename T, int W, int DIM>
 __global__ void __launch_bounds__(256)
     k_interp(const cx_t<T>* __restrict__ fine, const ushort4* __restrict__ l0, const T* __restrict__ psi,
-             const T* __restrict__ scale, cx_t<T>* __restrict__ cout, cx_t<T>* __restrict__ czout,
-             long long count, GridDims g) {
+             const T* __restrict__ scale, cx_t<T>* __restrict__ cout, long long count, GridDims g) {
   using C = cx_t<T>;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+  constexpr int XL = W <= 8 ? 8 : 16;
+  const int lane = threadIdx.x & 31;
+  const int rx = lane % XL;
+  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / XL;
+  const bool valid = i0 < count;  // lanes past the end compute a copy of the last node
+  const long long i = valid ? i0 : count - 1;
   const ushort4 s = l0[i];
   const T* ps = psi + i * 3 * W;
-  T kx[W], ky[W];
+  T ky[W], kz[W];
+  load_taps<T, W>(ps + W, ky);
+  if (DIM == 3) load_taps<T, W>(ps + 2 * W, kz);
+  const bool on = rx < W;
+  const T kx = on ? __ldg(ps + rx) : (T)0;
+  const int xx = wrap1(s.x + (on ? rx : 0), g.nf[0]);
+  int yoff[W];  // row offsets within a plane (a plane holds < 2^31 cells)
 #pragma unroll
-  for (int a = 0; a < W; ++a) {
-    kx[a] = ps[a];
-    ky[a] = ps[W + a];
-  }
+  for (int ay = 0; ay < W; ++ay) yoff[ay] = wrap1(s.y + ay, g.nf[1]) * g.nf[0];
   T ar = 0, ai = 0;
   if (DIM == 3) {
-#pragma unroll 1
+    const long long plane = (long long)g.nf[1] * g.nf[0];
+#pragma unroll
     for (int az = 0; az < W; ++az) {
-      const T wz = ps[2 * W + az];
-      const long long zoff = (long long)wrap1(s.z + az, g.nf[2]) * g.nf[1];
+      const C* zp = fine + wrap1(s.z + az, g.nf[2]) * plane + xx;
       T zr = 0, zi = 0;
 #pragma unroll
       for (int ay = 0; ay < W; ++ay) {
-        const C* row = fine + (zoff + wrap1(s.y + ay, g.nf[1])) * g.nf[0];
-        T rr = 0, ri = 0;
-#pragma unroll
-        for (int ax = 0; ax < W; ++ax) {
-          const C v = __ldg(row + wrap1(s.x + ax, g.nf[0]));
-          rr += kx[ax] * v.x;
-          ri += kx[ax] * v.y;
-        }
-        zr += ky[ay] * rr;
-        zi += ky[ay] * ri;
+        const C v = __ldg(zp + yoff[ay]);
+        zr += ky[ay] * v.x;
+        zi += ky[ay] * v.y;
       }
-      ar += wz * zr;
-      ai += wz * zi;
+      ar += kz[az] * zr;
+      ai += kz[az] * zi;
     }
   } else {
 #pragma unroll
     for (int ay = 0; ay < W; ++ay) {
-      const C* row = fine + (long long)wrap1(s.y + ay, g.nf[1]) * g.nf[0];
-      T rr = 0, ri = 0;
-#pragma unroll
-      for (int ax = 0; ax < W; ++ax) {
-        const C v = __ldg(row + wrap1(s.x + ax, g.nf[0]));
-        rr += kx[ax] * v.x;
-        ri += kx[ax] * v.y;
-      }
-      ar += ky[ay] * rr;
-      ai += ky[ay] * ri;
+      const C v = __ldg(fine + xx + yoff[ay]);
+      ar += ky[ay] * v.x;
+      ai += ky[ay] * v.y;
     }
   }
-  const T sc = scale[i];
-  const C c = cmk<C>(sc * ar, sc * ai);
-  cout[i] = c;
-  // factors of the spread's owned axis (z in 3D, y in 2D)
-  const T* po = ps + (DIM == 3 ? 2 : 1) * W;
+  ar *= kx;
+  ai *= kx;
 #pragma unroll
-  for (int a = 0; a < W; ++a) czout[i * W + a] = cmk<C>(c.x * po[a], c.y * po[a]);
-}
-
-// c_q -> c_q psi_owned (the type-1 stage run on its own, from given node values)
-template <typename T, int W, int DIM>
-__global__ void k_expand(const cx_t<T>* __restrict__ c, const T* __restrict__ psi, cx_t<T>* __restrict__ czout,
-                         long long count) {
-  using C = cx_t<T>;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const C cq = c[i];
-  const T* po = psi + i * 3 * W + (DIM == 3 ? 2 : 1) * W;
-#pragma unroll
-  for (int a = 0; a < W; ++a) czout[i * W + a] = cmk<C>(cq.x * po[a], cq.y * po[a]);
+  for (int o = XL / 2; o > 0; o >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, o);
+    ai += __shfl_xor_sync(0xffffffffu, ai, o);
+  }
+  if (rx == 0 && valid) {
+    const T sc = scale[i];
+    cout[i] = cmk<C>(sc * ar, sc * ai);
+  }
 }
 
 // ---- spreading (type 1) ------------------------------------------------------------------------
@@ -141,54 +161,78 @@ struct SpreadArgs {
   int nunits;
   int* counter;             // next unit to take (zeroed before the launch)
   const int4* visits;       // (node, ox, oy, oz): starts relative to the tile origin
-  const void* cz;           // [node][w] c psi_owned
+  const void* c;            // [node] c_q
   const void* psi;          // [node][3][w]
   void* fine;
-  void* partial;            // [slot][plane cells]
+  void* partial;            // [slot][TY][TX]
 };
 
-// per-warp shared memory of k_spread: the owned plane and a stage of 32 nodes
+// per-warp shared memory of k_spread: the plane buffer and a stage of 32 nodes
+template <typename T>
+struct alignas(16) NodeHead {
+  cx_t<T> cz;     // c_q psi_z(plane) (3D), c_q (2D)
+  int base;       // buffer index of the footprint's first cell
+  unsigned mask;  // taps inside the tile: bit t (x tap t), bit 16 + t (y tap t)
+};
 template <typename T, int W>
 struct alignas(16) WarpStage {
+  static constexpr int XL = W <= 8 ? 8 : 16, RL = 32 / XL, MR = (W + RL - 1) / RL, PW = MR * RL;
   T px[32][W];
-  T py[32][W];
-  cx_t<T> cz[32];
-  int2 o[32];
+  T py[32][PW];  // psi_y regrouped per lane row: py[j][MR r + m] = psi_y(r + RL m), 0 past w
+  NodeHead<T> hd[32];
 };
+static_assert(sizeof(WarpStage<float, 8>) == spread_stage_bytes(8, 4), "stage size");
+static_assert(sizeof(WarpStage<float, 6>) == spread_stage_bytes(6, 4), "stage size");
+static_assert(sizeof(WarpStage<double, 14>) == spread_stage_bytes(14, 8), "stage size");
+static_assert(sizeof(WarpStage<double, 10>) == spread_stage_bytes(10, 8), "stage size");
 
-// Spread, one warp per work unit = (tile, owned plane).  The plane's cells are touched by
-// no other unit, so the warp accumulates them in its own shared-memory buffer with plain
-// read-modify-writes and writes them once.  Persistent: warps take units from a counter
-// (largest first).  Lanes stage 32 nodes at a time (kernel values along x and y, c psi
-// along the owned axis, starts), then each node adds c psi_owned psi_y psi_x to the cells
-// of its footprint in the plane (lanes: x fastest, then y rows).  Consecutive nodes with
-// the same (oy, ox) are summed in registers and written once per run.  In 2D the owned
-// plane is a y-row.
+// taps t in [0, w) of a footprint starting at o that land inside [0, T), as a bit mask
+__device__ __forceinline__ unsigned tap_mask(int o, int T, int w) {
+  const int lo = o < 0 ? -o : 0;
+  const int hi = T - o < w ? T - o : w;
+  if (hi <= lo) return 0u;
+  return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+// Spread, one warp per work unit.  A unit is a (tile, z-plane) in 3D and a whole tile in
+// 2D: a plane of TY x TX fine cells that no other unit writes, so the warp accumulates it
+// in its own shared-memory buffer with plain read-modify-writes and writes it once.
+// Persistent: warps take units from a counter (largest first).  Lanes stage 32 nodes at a
+// time (kernel values along x and y, c_q psi_z(plane), the footprint's first cell and the
+// mask of its taps inside the tile), then the warp adds each node's w x w footprint
+// c psi_y psi_x into the plane: lanes are (x, row) pairs, XL along x and 32/XL rows per
+// instruction.  Long units are split into pieces that write partial planes (k_reduce).
 template <typename T, int W, int DIM>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
   using C = cx_t<T>;
-  constexpr int XL = W <= 8 ? 8 : 16;    // lanes along x
-  constexpr int RL = 32 / XL;            // y rows per warp instruction (3D)
-  constexpr int MR = (W + RL - 1) / RL;  // row iterations per (node, plane)
-  constexpr int NM = DIM == 3 ? MR : 1;
+  using S = WarpStage<T, W>;
+  constexpr int XL = S::XL, RL = S::RL, MR = S::MR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
   const int RS = spread_row_stride(TX);
-  const bool swz = spread_swizzle(TX);
-  const int PSZ = DIM == 3 ? TY * RS : RS;  // cells of one plane buffer
+  const int PSZ = TY * RS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t per_warp = spread_warp_bytes(PSZ * sizeof(C), sizeof(WarpStage<T, W>));
+  const size_t per_warp = spread_warp_bytes(PSZ * sizeof(C), sizeof(S));
   C* plane = reinterpret_cast<C*>(smem_raw + warp * per_warp);
-  WarpStage<T, W>* stage = reinterpret_cast<WarpStage<T, W>*>(smem_raw + warp * per_warp + ((PSZ * sizeof(C) + 15) & ~(size_t)15));
+  S* stage = reinterpret_cast<S*>(smem_raw + warp * per_warp + ((PSZ * sizeof(C) + 15) & ~(size_t)15));
   const int nfx = a.g.nf[0], nfy = a.g.nf[1], nfz = a.g.nf[2];
-  const bool wrx = a.ntile[0] == 1, wry = a.ntile[1] == 1;
-  const bool wrp = DIM == 3 ? a.ntile[2] == 1 : a.ntile[1] == 1;  // owned axis wraps in the tile
-  const int nfp = DIM == 3 ? nfz : nfy;
+  // an axis held by a single tile wraps around inside it
+  const bool wrx = a.ntile[0] == 1, wry = a.ntile[1] == 1, wrz = DIM == 3 && a.ntile[2] == 1;
+  const bool wrap = wrx || wry;
   const int4* __restrict__ vis = a.visits;
-  const C* __restrict__ czg = static_cast<const C*>(a.cz);
+  const C* __restrict__ cg = static_cast<const C*>(a.c);
   const T* __restrict__ psi = static_cast<const T*>(a.psi);
   const int rx = lane % XL, ry = lane / XL;
-  const int ncell = DIM == 3 ? TX * TY : TX;  // cells of one owned plane
+  const int rxc = rx < W ? rx : W - 1;
+  // this lane's cell of the footprint per row iteration: required mask bits, buffer offset
+  unsigned lbit[MR];
+  int loff[MR];
+#pragma unroll
+  for (int m = 0; m < MR; ++m) {
+    const int r = ry + RL * m;
+    lbit[m] = (rx < W && r < W) ? ((1u << rx) | (1u << (16 + r))) : 0xFFFFFFFFu;
+    loff[m] = r * RS + rx;
+  }
 
   for (;;) {
     int u = 0;
@@ -199,108 +243,111 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
     for (int i = lane; i < PSZ; i += 32) plane[i] = cmk<C>((T)0, (T)0);
     __syncwarp();
     const int p = U.plane;
-    T ar[NM], ai[NM];
-#pragma unroll
-    for (int m = 0; m < NM; ++m) ar[m] = ai[m] = (T)0;
-    int run_x = INT_MIN, run_y = 0;
-    C* cellp[NM];
-    bool okp[NM];
     for (int kb = U.lo; kb < U.hi; kb += 32) {
       const int cnt = min(32, U.hi - kb);
       if (lane < cnt) {
         const int4 e = vis[kb + lane];
         const size_t node = (size_t)e.x;
-        int az = p - (DIM == 3 ? e.w : e.z);
-        if (wrp) az = az < 0 ? az + nfp : (az >= nfp ? az - nfp : az);
-        const bool use = az >= 0 && az < W;
-        stage->cz[lane] = use ? czg[node * W + az] : cmk<C>((T)0, (T)0);
-        stage->o[lane] = make_int2(use ? e.y : INT_MIN + 1, e.z);
         const T* ps = psi + node * 3 * W;
-#pragma unroll
-        for (int q = 0; q < W; ++q) stage->px[lane][q] = ps[q];
+        bool use = true;
+        T pz = (T)1;
         if (DIM == 3) {
-#pragma unroll
-          for (int q = 0; q < W; ++q) stage->py[lane][q] = ps[W + q];
+          int az = p - e.w;
+          if (wrz) az = az < 0 ? az + nfz : (az >= nfz ? az - nfz : az);
+          use = az >= 0 && az < W;
+          pz = use ? ps[2 * W + az] : (T)0;
         }
+        const C cq = cg[node];
+        T tx[W], ty[W];
+        load_taps<T, W>(ps, tx);
+        load_taps<T, W>(ps + W, ty);
+        const unsigned xm = wrx ? (1u << W) - 1u : tap_mask(e.y, TX, W);
+        const unsigned ym = wry ? (1u << W) - 1u : tap_mask(e.z, TY, W);
+        NodeHead<T> h;
+        h.cz = cmk<C>(cq.x * pz, cq.y * pz);
+        h.base = e.z * RS + e.y;
+        h.mask = use ? (xm | (ym << 16)) : 0u;
+        stage->hd[lane] = h;
+#pragma unroll
+        for (int q = 0; q < W; ++q) stage->px[lane][q] = tx[q];
+#pragma unroll
+        for (int r = 0; r < RL; ++r)
+#pragma unroll
+          for (int m = 0; m < MR; ++m) stage->py[lane][MR * r + m] = r + RL * m < W ? ty[r + RL * m] : (T)0;
       }
       __syncwarp();
-      for (int j = 0; j < cnt; ++j) {
-        const int2 o = stage->o[j];
-        if (o.x == INT_MIN + 1) continue;  // wrapping tiles only: this node misses plane p
-        if (o.x != run_x || o.y != run_y) {
-          if (run_x != INT_MIN) {
+      if (!wrap) {
+        for (int j = 0; j < cnt; ++j) {
+          const NodeHead<T> h = stage->hd[j];
+          const T wx = stage->px[j][rxc];
+          T wy[MR];
 #pragma unroll
-            for (int m = 0; m < NM; ++m)
-              if (okp[m]) {
-                C cur = *cellp[m];
-                cur.x += ar[m];
-                cur.y += ai[m];
-                *cellp[m] = cur;
-              }
+          for (int m = 0; m < MR; ++m) wy[m] = stage->py[j][MR * ry + m];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) ar[m] = ai[m] = (T)0;
+          for (int m = 0; m < MR; ++m) {
+            if ((h.mask & lbit[m]) == lbit[m]) {
+              const T w = wy[m] * wx;
+              C* cell = plane + h.base + loff[m];
+              C v = *cell;
+              v.x += h.cz.x * w;
+              v.y += h.cz.y * w;
+              *cell = v;
+            }
           }
-          // cells of this lane for the new footprint
-          run_x = o.x;
-          run_y = o.y;
-          int xx = o.x + rx;
+          __syncwarp();  // the next node's cells may belong to other lanes
+        }
+      } else {
+        for (int j = 0; j < cnt; ++j) {
+          const NodeHead<T> h = stage->hd[j];
+          if (h.mask == 0u) continue;  // this node misses plane p (uniform over the warp)
+          const int4 e = vis[kb + j];
+          const T wx = stage->px[j][rxc];
+          int xx = e.y + rx;
           if (wrx && xx < 0) xx += nfx;
           const bool okx = rx < W && (unsigned)xx < (unsigned)TX;
 #pragma unroll
-          for (int m = 0; m < NM; ++m) {
+          for (int m = 0; m < MR; ++m) {
             const int r = ry + RL * m;
-            int yy = o.y + r;
+            int yy = e.z + r;
             if (wry && yy < 0) yy += nfy;
-            okp[m] = okx && (DIM == 3 ? (r < W && (unsigned)yy < (unsigned)TY) : ry == 0);
-            cellp[m] = plane + (DIM == 3 ? spread_cell(okp[m] ? yy : 0, okp[m] ? xx : 0, RS, swz) : (okp[m] ? xx : 0));
+            if (okx && r < W && (unsigned)yy < (unsigned)TY) {
+              const T w = stage->py[j][MR * ry + m] * wx;
+              C* cell = plane + yy * RS + xx;
+              C v = *cell;
+              v.x += h.cz.x * w;
+              v.y += h.cz.y * w;
+              *cell = v;
+            }
           }
-        }
-        const C czv = stage->cz[j];
-        const T wx = rx < W ? stage->px[j][rx] : (T)0;
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-          const int r = ry + RL * m;
-          const T w = DIM == 3 ? (r < W ? stage->py[j][r] : (T)0) * wx : wx;
-          ar[m] += czv.x * w;
-          ai[m] += czv.y * w;
+          __syncwarp();
         }
       }
       __syncwarp();
-    }
-    if (run_x != INT_MIN) {
-#pragma unroll
-      for (int m = 0; m < NM; ++m)
-        if (okp[m]) {
-          C cur = *cellp[m];
-          cur.x += ar[m];
-          cur.y += ai[m];
-          *cellp[m] = cur;
-        }
     }
     __syncwarp();
     // write the plane (or this unit's partial plane)
     const int tx = U.tile % a.ntile[0];
     const int ty = (U.tile / a.ntile[0]) % a.ntile[1];
     const int tz = U.tile / (a.ntile[0] * a.ntile[1]);
-    const int T0x = tile_origin(tx, TX, a.ntile[0], nfx);
-    const int T0y = tile_origin(ty, TY, a.ntile[1], nfy);
-    const int T0z = tile_origin(tz, TZ, a.ntile[2], nfz);
     if (U.slot < 0) {
-      C* fine = static_cast<C*>(a.fine);
-      for (int i = lane; i < ncell; i += 32) {
-        const int lx = i % TX, ly = DIM == 3 ? i / TX : p;
-        const int lz = DIM == 3 ? p : 0;
-        const int gx = T0x + lx, gy = T0y + ly, gz = T0z + lz;
-        const long long off =
-            ((long long)(gz >= nfz ? gz - nfz : gz) * nfy + (gy >= nfy ? gy - nfy : gy)) * nfx + (gx >= nfx ? gx - nfx : gx);
-        fine[off] = plane[DIM == 3 ? spread_cell(ly, lx, RS, swz) : lx];
+      const int T0x = tile_origin(tx, TX, a.ntile[0], nfx);
+      const int T0y = tile_origin(ty, TY, a.ntile[1], nfy);
+      int gz = DIM == 3 ? tile_origin(tz, TZ, a.ntile[2], nfz) + p : 0;
+      gz -= gz >= nfz ? nfz : 0;
+      C* fine = static_cast<C*>(a.fine) + (long long)gz * nfy * nfx;
+      for (int ly = 0; ly < TY; ++ly) {
+        int gy = T0y + ly;
+        gy -= gy >= nfy ? nfy : 0;
+        for (int lx = lane; lx < TX; lx += 32) {
+          int gx = T0x + lx;
+          gx -= gx >= nfx ? nfx : 0;
+          fine[(long long)gy * nfx + gx] = plane[ly * RS + lx];
+        }
       }
     } else {
-      C* part = static_cast<C*>(a.partial) + (long long)U.slot * ncell;
-      for (int i = lane; i < ncell; i += 32) {
-        const int lx = i % TX, ly = i / TX;
-        part[i] = plane[DIM == 3 ? spread_cell(ly, lx, RS, swz) : lx];
-      }
+      C* part = static_cast<C*>(a.partial) + (long long)U.slot * TX * TY;
+      for (int ly = 0; ly < TY; ++ly)
+        for (int lx = lane; lx < TX; lx += 32) part[ly * TX + lx] = plane[ly * RS + lx];
     }
     __syncwarp();
   }
@@ -312,11 +359,11 @@ __global__ void k_reduce(const SplitUnit* __restrict__ split, const cx_t<T>* __r
                          cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx, int nty, int ntz) {
   using C = cx_t<T>;
   const SplitUnit st = split[blockIdx.x];
-  const int ncell = DIM == 3 ? TX * TY : TX;
+  const int ncell = TX * TY;
   const int tx = st.tile % ntx, ty = (st.tile / ntx) % nty, tz = st.tile / (ntx * nty);
   const int ox = tile_origin(tx, TX, ntx, g.nf[0]);
   const int oy = tile_origin(ty, TY, nty, g.nf[1]);
-  const int oz = tile_origin(tz, TZ, ntz, g.nf[2]);
+  const int oz = DIM == 3 ? tile_origin(tz, TZ, ntz, g.nf[2]) : 0;
   for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
     T sr = 0, si = 0;
     for (int k = 0; k < st.nslots; ++k) {
@@ -325,7 +372,7 @@ __global__ void k_reduce(const SplitUnit* __restrict__ split, const cx_t<T>* __r
       si += v.y;
     }
     int gx = ox + i % TX;
-    int gy = oy + (DIM == 3 ? i / TX : st.plane);
+    int gy = oy + i / TX;
     int gz = oz + (DIM == 3 ? st.plane : 0);
     gx -= gx >= g.nf[0] ? g.nf[0] : 0;
     gy -= gy >= g.nf[1] ? g.nf[1] : 0;
@@ -338,19 +385,11 @@ __global__ void k_reduce(const SplitUnit* __restrict__ split, const cx_t<T>* __r
 template <typename T, int W, int DIM>
 int launch_interp(Plan& p, cudaStream_t s) {
   const long long cnt = p.Mh;
-  k_interp<T, W, DIM><<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+  constexpr int XL = W <= 8 ? 8 : 16;
+  if (cnt == 0) return DDI_OK;
+  k_interp<T, W, DIM><<<(unsigned)((cnt * XL + 255) / 256), 256, 0, s>>>(
       static_cast<const cx_t<T>*>(p.d_fine), static_cast<const ushort4*>(p.d_l0), static_cast<const T*>(p.d_psi),
-      static_cast<const T*>(p.d_scale), static_cast<cx_t<T>*>(p.d_c), static_cast<cx_t<T>*>(p.d_cz), cnt,
-      dims_of(p));
-  DDI_LAUNCH_CHECK();
-  return DDI_OK;
-}
-
-template <typename T, int W, int DIM>
-int launch_expand(Plan& p, cudaStream_t s) {
-  const long long cnt = p.Mh;
-  k_expand<T, W, DIM><<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
-      static_cast<const cx_t<T>*>(p.d_c), static_cast<const T*>(p.d_psi), static_cast<cx_t<T>*>(p.d_cz), cnt);
+      static_cast<const T*>(p.d_scale), static_cast<cx_t<T>*>(p.d_c), cnt, dims_of(p));
   DDI_LAUNCH_CHECK();
   return DDI_OK;
 }
@@ -392,7 +431,7 @@ int launch_spread(Plan& p, cudaStream_t s) {
   a.nunits = p.nunits;
   a.counter = p.d_counter;
   a.visits = p.d_visits;
-  a.cz = p.d_cz;
+  a.c = p.d_c;
   a.psi = p.d_psi;
   a.fine = p.d_fine;
   a.partial = p.d_partial;
@@ -435,7 +474,6 @@ int launch_spread(Plan& p, cudaStream_t s) {
   }
 
 DDI_WIDTH_SWITCH(launch_interp)
-DDI_WIDTH_SWITCH(launch_expand)
 DDI_WIDTH_SWITCH(launch_spread)
 DDI_WIDTH_SWITCH(configure_spread)
 
@@ -451,7 +489,7 @@ int configure_kernels(Plan& p) {
 // tile: the best of `reps` timed launches after one untimed one, on zeroed node values
 // (the cost depends on the node set and the tile, not on the values).
 int time_spread(Plan& p, cudaStream_t s, int reps, float* ms) {
-  DDI_CUDA(cudaMemsetAsync(p.d_cz, 0, p.cx_size() * (size_t)p.Mh * p.w, s));
+  DDI_CUDA(cudaMemsetAsync(p.d_c, 0, p.cx_size() * (size_t)p.Mh, s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -498,7 +536,6 @@ int run_type1(Plan& p, T* phi, cudaStream_t s) {
 
 template <typename T>
 int run_type1_from_c(Plan& p, T* phi, cudaStream_t s) {
-  DDI_TRY((p.dim == 3 ? launch_expand_w<T, 3>(p, s) : launch_expand_w<T, 2>(p, s)));
   return run_type1<T>(p, phi, s);
 }
 

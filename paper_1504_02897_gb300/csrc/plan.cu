@@ -79,7 +79,7 @@ void choose_tile(Plan& p) {
       want[0] = 16; want[1] = 16; want[2] = 16;
     }
   } else {
-    want[0] = 64; want[1] = 64; want[2] = 1;
+    want[0] = 32; want[1] = 16; want[2] = 1;
   }
   for (int d = 0; d < 3; ++d) {
     if (p.desc.tile[d] > 0) want[d] = p.desc.tile[d];
@@ -87,11 +87,11 @@ void choose_tile(Plan& p) {
     p.tile[d] = d < p.dim ? pick(want[d], need, p.nf[d]) : 1;
     p.ntile[d] = p.nf[d] / p.tile[d];
   }
-  p.npl = p.dim == 3 ? p.tile[2] : p.tile[1];
+  p.npl = p.dim == 3 ? p.tile[2] : 1;
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_cz,  p.d_deconv, p.d_fine,  p.d_partial,
+  void* ptrs[] = {p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_fine,  p.d_partial,
                   p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
                   p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out};
   for (void* q : ptrs)
@@ -121,7 +121,7 @@ int build_spread(Plan& p, cudaStream_t stream) {
   const ddi_plan_desc& d = p.desc;
   const int dim = p.dim, W = p.w;
   const size_t rs = p.real_size(), cs = p.cx_size();
-  const size_t warp_bytes = spread_warp_bytes(p.spread_plane_cells() * cs, 2 * 32 * W * rs + 32 * (cs + 8));
+  const size_t warp_bytes = spread_warp_bytes(p.spread_plane_cells() * cs, spread_stage_bytes(W, rs));
   if (warp_bytes * (kSpreadThreads / 32) > 200 * 1024) {
     set_error("spread plane needs %zu bytes of shared memory per warp; choose a smaller tile", warp_bytes);
     return DDI_ERR_ARG;
@@ -137,8 +137,8 @@ int build_spread(Plan& p, cudaStream_t stream) {
   const size_t before = p.bytes;
 
   // spread visit lists: per tile, the nodes whose taps reach it with their starts relative
-  // to the tile, ordered by (o_owned, o_row, ox) so that each owned plane's nodes are one
-  // contiguous range
+  // to the tile, ordered by (oz, oy, ox) so that each z-plane's nodes are one contiguous
+  // range (3D)
   const int ntiles = p.ntile[0] * p.ntile[1] * p.ntile[2];
   std::vector<std::vector<std::pair<int64_t, int4>>> lists(ntiles);
   for (int64_t i = 0; i < p.Mh; ++i) {
@@ -174,7 +174,8 @@ int build_spread(Plan& p, cudaStream_t stream) {
     total += (long long)L.size();
   }
   p.visits = total;
-  const bool wrap_owned = dim == 3 ? p.ntile[2] == 1 : p.ntile[1] == 1;
+  // 2D: one unit per tile (the whole tile is the plane); 3D: one per z-plane
+  const bool wrap_owned = dim == 3 ? p.ntile[2] == 1 : true;
   std::vector<int4> visits;
   visits.reserve(total);
   // work units (tile, owned plane): the list entries whose taps along the owned axis cover
@@ -185,7 +186,7 @@ int build_spread(Plan& p, cudaStream_t stream) {
     const int beg = (int)visits.size();
     for (auto& e : lists[t]) visits.push_back(e.second);
     const int end = (int)visits.size();
-    auto owned = [&](int k) { return dim == 3 ? visits[k].w : visits[k].z; };
+    auto owned = [&](int k) { return visits[k].w; };
     for (int pl = 0; pl < p.npl; ++pl) {
       int lo = beg, hi = end;
       if (!wrap_owned) {
@@ -234,7 +235,7 @@ int build_spread(Plan& p, cudaStream_t stream) {
   DDI_TRY(upload(p, (void**)&p.d_visits, visits, "visit lists", stream));
   DDI_TRY(upload(p, (void**)&p.d_units, work, "work units", stream));
   DDI_TRY(upload(p, (void**)&p.d_split, split, "split units", stream));
-  const size_t plane_cells = dim == 3 ? (size_t)p.tile[0] * p.tile[1] : (size_t)p.tile[0];
+  const size_t plane_cells = (size_t)p.tile[0] * p.tile[1];
   DDI_TRY(dev_alloc(p, &p.d_partial, cs * plane_cells * std::max(1, p.nslots), "partial planes"));
   p.spread_bytes = p.bytes - before;
   // the host vectors above die with this frame
@@ -338,7 +339,6 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
   DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
   DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
-  DDI_TRY(dev_alloc(p, &p.d_cz, cs * p.Mh * W, "node plane factors"));
   DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
   for (int a = 0; a < 3; ++a) {
     if (p.nf[a] > 1) DDI_TRY(make_twiddles(p, p.nf[a]));

@@ -3,7 +3,8 @@
     python -m paper_1504_02897_gb300.drive [--precision fp32|fp64] [--repeat 3] [--n 128]
 
 Builds the plan of bench.py's workload (8-Gaussian mixture, seed 0, on [-12,12)^3, axis
-(sin 30, 0, cos 30), quadrature n x n/2 x n) and calls ddi_apply `repeat` times.
+(sin 30, 0, cos 30), quadrature n x n/2 x n, autotuned spread tile) and calls ddi_apply
+`repeat` times.
 """
 import argparse
 import os
@@ -17,6 +18,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--autotune", type=int, default=1, help="1: spread tile by the autotuner (as bench.py)")
     args = ap.parse_args()
     import torch
     from paper_1504_02897_gb300 import build, ddi, synth
@@ -25,13 +27,14 @@ def main():
     n = args.n
     w = synth.gaussian_mixture_density(n, 12.0, seed=0)
     prec = ddi.FP32 if args.precision == "fp32" else ddi.FP64
-    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=prec, nr=n, ntheta=n // 2, nphi=n)
+    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=prec, nr=n, ntheta=n // 2, nphi=n,
+                    tile=(-1, 0, 0) if args.autotune else None)
     rho = torch.from_numpy(w["rho"]).to("cuda", plan.real_dtype)
     out = torch.empty_like(rho)
     for _ in range(args.repeat):
         plan.apply(rho, out)
     torch.cuda.synchronize()
-    print("ok", float(out.abs().max()))
+    print("ok", float(out.abs().max()), "tile", list(plan.info.tile))
 
 
 if __name__ == "__main__":

@@ -321,7 +321,8 @@ def main():
     if os.path.exists(prof):
         try:
             tr = json.load(open(prof))
-            if tr.get("kernel") == dominant and tr.get("source_hash") == _kernel_hash():
+            if (tr.get("kernel") == dominant and tr.get("source_hash") == _kernel_hash()
+                    and tr.get("tile", list(info.tile)) == list(info.tile)):
                 traffic = tr.get("bytes_per_launch")
         except Exception:
             traffic = None

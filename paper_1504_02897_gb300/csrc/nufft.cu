@@ -93,8 +93,9 @@ __device__ __forceinline__ void load_taps(const T* __restrict__ src, T (&dst)[W]
 // lanes of a node read each footprint row of the fine grid as one contiguous segment,
 // accumulate the psi_y (and psi_z) weighted sums in registers, and the node's value is
 // the psi_x-weighted sum over its lanes (shuffle reduction).
+// (at most 64 registers in FP32, so that 4 CTAs per SM keep enough loads in flight)
 template <typename T, int W, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_interp(const cx_t<T>* __restrict__ fine, const ushort4* __restrict__ l0, const T* __restrict__ psi,
              const T* __restrict__ scale, cx_t<T>* __restrict__ cout, long long count, GridDims g) {
   using C = cx_t<T>;
@@ -353,32 +354,43 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs a) {
   }
 }
 
-// Sums the partial planes of split units into the fine grid.
+// Sums the partial planes of split units into the fine grid: one thread per (split unit,
+// cell), blockIdx.y = split unit - split0, partials summed in slot order (deterministic).
 template <typename T, int DIM>
-__global__ void k_reduce(const SplitUnit* __restrict__ split, const cx_t<T>* __restrict__ partial,
-                         cx_t<T>* __restrict__ fine, GridDims g, int TX, int TY, int TZ, int ntx, int nty, int ntz) {
+__global__ void __launch_bounds__(256)
+    k_reduce(const SplitUnit* __restrict__ split, const cx_t<T>* __restrict__ partial, cx_t<T>* __restrict__ fine,
+             GridDims g, int TX, int TY, int TZ, int ntx, int nty, int ntz, int split0) {
   using C = cx_t<T>;
-  const SplitUnit st = split[blockIdx.x];
   const int ncell = TX * TY;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell) return;
+  const SplitUnit st = split[split0 + blockIdx.y];
   const int tx = st.tile % ntx, ty = (st.tile / ntx) % nty, tz = st.tile / (ntx * nty);
-  const int ox = tile_origin(tx, TX, ntx, g.nf[0]);
-  const int oy = tile_origin(ty, TY, nty, g.nf[1]);
-  const int oz = DIM == 3 ? tile_origin(tz, TZ, ntz, g.nf[2]) : 0;
-  for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
-    T sr = 0, si = 0;
-    for (int k = 0; k < st.nslots; ++k) {
-      const C v = partial[(long long)(st.slot0 + k) * ncell + i];
-      sr += v.x;
-      si += v.y;
+  const C* src = partial + (long long)st.slot0 * ncell + i;
+  T sr = 0, si = 0;
+  int k = 0;
+  for (; k + 4 <= st.nslots; k += 4) {
+    C v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __ldg(src + (long long)(k + q) * ncell);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sr += v[q].x;
+      si += v[q].y;
     }
-    int gx = ox + i % TX;
-    int gy = oy + i / TX;
-    int gz = oz + (DIM == 3 ? st.plane : 0);
-    gx -= gx >= g.nf[0] ? g.nf[0] : 0;
-    gy -= gy >= g.nf[1] ? g.nf[1] : 0;
-    gz -= gz >= g.nf[2] ? g.nf[2] : 0;
-    fine[((long long)gz * g.nf[1] + gy) * g.nf[0] + gx] = cmk<C>(sr, si);
   }
+  for (; k < st.nslots; ++k) {
+    const C v = __ldg(src + (long long)k * ncell);
+    sr += v.x;
+    si += v.y;
+  }
+  int gx = tile_origin(tx, TX, ntx, g.nf[0]) + i % TX;
+  int gy = tile_origin(ty, TY, nty, g.nf[1]) + i / TX;
+  int gz = (DIM == 3 ? tile_origin(tz, TZ, ntz, g.nf[2]) : 0) + (DIM == 3 ? st.plane : 0);
+  gx -= gx >= g.nf[0] ? g.nf[0] : 0;
+  gy -= gy >= g.nf[1] ? g.nf[1] : 0;
+  gz -= gz >= g.nf[2] ? g.nf[2] : 0;
+  fine[((long long)gz * g.nf[1] + gy) * g.nf[0] + gx] = cmk<C>(sr, si);
 }
 
 // ---- launch helpers ----------------------------------------------------------------------------
@@ -443,10 +455,13 @@ int launch_spread(Plan& p, cudaStream_t s) {
   DDI_LAUNCH_CHECK();
   p.mark("spread", s);
   if (p.nsplit > 0) {
-    k_reduce<T, DIM><<<p.nsplit, 256, 0, s>>>(p.d_split, static_cast<const cx_t<T>*>(p.d_partial),
-                                              static_cast<cx_t<T>*>(p.d_fine), dims_of(p), p.tile[0], p.tile[1],
-                                              p.tile[2], p.ntile[0], p.ntile[1], p.ntile[2]);
-    DDI_LAUNCH_CHECK();
+    for (int s0 = 0; s0 < p.nsplit; s0 += 65535) {
+      const dim3 grid((unsigned)((p.tile[0] * p.tile[1] + 255) / 256), (unsigned)std::min(65535, p.nsplit - s0));
+      k_reduce<T, DIM><<<grid, 256, 0, s>>>(p.d_split, static_cast<const cx_t<T>*>(p.d_partial),
+                                            static_cast<cx_t<T>*>(p.d_fine), dims_of(p), p.tile[0], p.tile[1],
+                                            p.tile[2], p.ntile[0], p.ntile[1], p.ntile[2], s0);
+      DDI_LAUNCH_CHECK();
+    }
     p.mark("spread_reduce", s);
   }
   return DDI_OK;

@@ -19,6 +19,7 @@ def main():
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--autotune", type=int, default=1, help="1: spread tile by the autotuner (as bench.py)")
+    ap.add_argument("--tile", default="", help="fixed spread tile x,y,z (overrides --autotune)")
     args = ap.parse_args()
     import torch
     from paper_1504_02897_gb300 import build, ddi, synth
@@ -28,7 +29,8 @@ def main():
     w = synth.gaussian_mixture_density(n, 12.0, seed=0)
     prec = ddi.FP32 if args.precision == "fp32" else ddi.FP64
     plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=prec, nr=n, ntheta=n // 2, nphi=n,
-                    tile=(-1, 0, 0) if args.autotune else None)
+                    tile=tuple(int(v) for v in args.tile.split(",")) if args.tile
+                    else ((-1, 0, 0) if args.autotune else None))
     rho = torch.from_numpy(w["rho"]).to("cuda", plan.real_dtype)
     out = torch.empty_like(rho)
     for _ in range(args.repeat):

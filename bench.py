@@ -202,8 +202,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ddi3d_128", choices=["ddi3d_128", "batch2d_96"],
-                    help="ddi3d_128: the headline 3D workload; batch2d_96: 96 2D densities in one batch")
+    ap.add_argument("--workload", default="ddi3d_128", choices=["ddi3d_128", "batch2d_96", "tsfp128", "gs128", "grad128"],
+                    help="ddi3d_128: the headline 3D workload; batch2d_96: 96 2D densities in one batch; "
+                         "tsfp128 / gs128 / grad128: the GPE step, ground state and trap gradient at 128^3")
+    ap.add_argument("--fp64-check", type=int, default=1, help="grad128: also run the FP64 path for its error")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -211,6 +213,9 @@ def main():
         return
     if args.workload == "batch2d_96":
         bench_batch2d(args)
+        return
+    if args.workload in ("tsfp128", "gs128", "grad128"):
+        bench_gpe(args)
         return
 
     import numpy as np
@@ -480,6 +485,116 @@ def bench_batch2d(args):
                 "d2h_bytes_per_step": 4 * grid_pts},
         "clocks": clocks,
     }
+    print(json.dumps(out))
+
+
+def bench_gpe(args):
+    """GPE workloads at 128^3 on [-10,10)^3, V = (x^2 + y^2 + 4 z^2)/2, beta = 207.16,
+    lambda = 0.16 beta, dipole axis z, FP32 path (FP64 reductions), autotuned spread tile:
+      tsfp128  one step = one Strang TSFP step (Eq. tssp2, Case I; dt = 1e-3), the DDI of
+               |psi_1|^2 included; psi0 = the trap Gaussian with a seeded 5% perturbation
+      gs128    the normalised gradient flow (backward Euler, dt = 0.01) from the trap
+               Gaussian until |E^{n+1} - E^n| < 1e-10 (checked every 10 steps)
+      grad128  J = h^3 sum z^2 |psi_T|^2 after 400 steps (dt = 1e-3) and dJ/dV by the
+               adjoint with checkpoints every 20 steps; with --fp64-check 1 the FP64 path
+               computes the same gradient for the FP32 one's error"""
+    import numpy as np
+    import torch
+    from paper_1504_02897_gb300 import build, ddi, synth
+
+    torch.cuda.set_device(0)
+    build.build()
+    ddi.load()
+    dev = torch.device("cuda", 0)
+    n, lo, ln = synth.box(128, 10.0, 3)
+    beta, lam = 207.16, 0.16 * 207.16
+    V64 = synth.harmonic_trap(n, lo, ln, (1.0, 1.0, 2.0))
+    peaks, src = _peaks()
+    peak = float(peaks["hbm_gbs"])
+
+    def plan_of(prec):
+        return ddi.Plan(3, n, lo, ln, (0.0, 0.0, 1.0), precision=prec, tile=(-1, 0, 0) if prec == ddi.FP32 else None)
+
+    plan = plan_of(ddi.FP32)
+    V = torch.from_numpy(V64).to(dev, torch.float32)
+    sampler = ClockSampler(0)
+    base = {"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic"}
+    cfg = {"grid": [128, 128, 128], "box": [-10.0, 10.0], "trap": [1, 1, 2], "beta": beta, "lambda": lam,
+           "axis": [0, 0, 1], "quadrature": [128, 64, 128], "spread_tile": list(plan.info.tile)}
+    if args.workload == "tsfp128":
+        dt = 1e-3
+        psi = torch.from_numpy(synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0), eps=0.05, seed=0)).to(dev, torch.complex64)
+        m0 = plan.gpe_energy(psi, V, beta, lam)["mass"]
+        for _ in range(args.warmup):
+            plan.gpe_step(psi, V, beta, lam, dt, 1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stream = torch.cuda.current_stream()
+        sampler.start()
+        time.sleep(0.3)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            plan.gpe_step(psi, V, beta, lam, dt, 1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        m1 = plan.gpe_energy(psi, V, beta, lam)["mass"]
+        step_bytes = 8 * 128 ** 3 + 2 * 4 * 256 ** 3 * 8 + 4 * 2 * 8 * 128 ** 3 + 50e6
+        out = dict(base, metric="TSFP steps/s at 128^3 (Eq. tssp2 Case I, DDI included, FP32-mixed)",
+                   value=1e3 / ms, unit="steps/s", steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+                   config=dict(cfg, workload="tsfp128_dt1e-3", dt=dt,
+                               mass_drift_per_step=abs(m1 - m0) / (args.steps + args.warmup),
+                               l2="inputs (67 MB of state) plus the 134 MB fine grid exceed L2"),
+                   step_roofline={"model_bytes": step_bytes, "achieved": step_bytes / (ms * 1e-3) / 1e9,
+                                  "peak": peak, "frac": step_bytes / (ms * 1e-3) / 1e9 / peak, "unit": "GB/s",
+                                  "peak_source": src + " hbm_gbs (copy)"},
+                   clocks=clocks)
+    elif args.workload == "gs128":
+        phi = torch.from_numpy(synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0))).to(dev, torch.complex64)
+        sampler.start()
+        t0 = time.perf_counter()
+        st = plan.ground_state(phi, V, beta, lam, 0.01, 1e-10, rule=ddi.STOP_ENERGY, max_steps=20000,
+                               check_every=10)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        out = dict(base, metric="ground state time at 128^3 (GF-BE, |dE| < 1e-10, FP32 + FP64 reductions)",
+                   value=wall, unit="s", higher_is_better=False, steps=st["steps"], warmup=0,
+                   ms_per_step=wall / max(1, st["steps"]) * 1e3,
+                   config=dict(cfg, workload="gs128_dt0.01", dt=0.01, converged=st["converged"],
+                               E=st["E"], mu=st["mu"], virial=st["virial"], mass=st["mass"],
+                               last_change=st["last_change"], inner_max=st["inner_max"]),
+                   clocks=clocks)
+    else:
+        dt, nsteps = 1e-3, 400
+        psi0_64 = synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0), eps=0.05, seed=0)
+        psi0 = torch.from_numpy(psi0_64).to(dev, torch.complex64)
+        ddi.trap_gradient(plan, psi0, V, beta, lam, dt, 20, checkpoint=20)  # warm-up
+        torch.cuda.synchronize()
+        sampler.start()
+        t0 = time.perf_counter()
+        J, g = ddi.trap_gradient(plan, psi0, V, beta, lam, dt, nsteps, checkpoint=20)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        extra = {}
+        if args.fp64_check:
+            del plan
+            torch.cuda.empty_cache()
+            p64 = plan_of(ddi.FP64)
+            t1 = time.perf_counter()
+            J64, g64 = ddi.trap_gradient(p64, torch.from_numpy(psi0_64).to(dev), torch.from_numpy(V64).to(dev),
+                                         beta, lam, dt, nsteps, checkpoint=20)
+            torch.cuda.synchronize()
+            extra = {"fp64_wall_s": time.perf_counter() - t1, "J_fp64": J64,
+                     "J_rel_err": abs(J - J64) / abs(J64),
+                     "grad_rel_err_linf": float((g.double() - g64).abs().max() / g64.abs().max())}
+        out = dict(base, metric="trap gradient time at 128^3 (400 TSFP steps + adjoint, checkpoints of 20, FP32-mixed)",
+                   value=wall, unit="s", higher_is_better=False, steps=nsteps, warmup=20,
+                   ms_per_step=wall / nsteps * 1e3,
+                   config=dict(cfg, workload="grad128_400steps_dt1e-3", dt=dt, J=J, **extra), clocks=clocks)
     print(json.dumps(out))
 
 

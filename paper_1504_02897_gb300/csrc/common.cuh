@@ -142,7 +142,7 @@ struct Plan {
   int spread_blocks = 1;
   int nsplit = 0, nslots = 0;
   int tw_n[8] = {};           // lengths of the twiddle tables below
-  void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n}
+  void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n} (FP32: n heads, then n tails)
   // GPE workspace
   void* d_psi1 = nullptr;     // cx [N]
   void* d_rho = nullptr;      // T [N]

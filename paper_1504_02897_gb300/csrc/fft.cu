@@ -14,6 +14,7 @@ struct PlainLines {
   C* data;
   LineGeom g;
   using Ref = long long;  // offset of the line's first element
+  static constexpr bool kPreciseTwiddles = true;  // the GPE's repeated transforms
   __host__ __device__ long long nlines() const { return g.nlines; }
   __device__ bool contig() const { return g.se == 1; }
   __device__ Ref ref(long long L) const { return line_off(g, L); }
@@ -31,27 +32,35 @@ int make_twiddles(Plan& p, int n) {
     set_error("too many distinct FFT lengths in one plan");
     return DDI_ERR_ARG;
   }
+  // FP64: e^{-2 pi i k / n} from FP64 libm.  FP32: head and tail of each component,
+  // [n] heads then [n] tails, so that a stage multiplies by the twiddle to FP64 accuracy:
+  // a rounded twiddle has |w| != 1 by up to 6e-8, and the same table in every transform
+  // would scale the data's norm by the same amount every time (a steady mass drift in
+  // long time-splitting runs)
   const size_t es = p.cx_size();
-  std::vector<unsigned char> host(es * n);
+  const size_t count = p.prec == DDI_FP64 ? (size_t)n : 2 * (size_t)n;
+  std::vector<unsigned char> host(es * count);
   for (int k = 0; k < n; ++k) {
-    // e^{-2 pi i k / n} from FP64 libm, rounded once to the working precision
     const double ang = (-2.0 * M_PI * (double)k) / (double)n;
     const double c = std::cos(ang), sn = std::sin(ang);
     if (p.prec == DDI_FP64) {
       double2 v = make_double2(c, sn);
       memcpy(host.data() + es * k, &v, es);
     } else {
-      float2 v = make_float2((float)c, (float)sn);
-      memcpy(host.data() + es * k, &v, es);
+      const float ch = (float)c, sh = (float)sn;
+      float2 hi = make_float2(ch, sh);
+      float2 lo = make_float2((float)(c - (double)ch), (float)(sn - (double)sh));
+      memcpy(host.data() + es * k, &hi, es);
+      memcpy(host.data() + es * (n + (size_t)k), &lo, es);
     }
   }
   void* d = nullptr;
-  if (cudaMalloc(&d, es * n) != cudaSuccess) {
+  if (cudaMalloc(&d, es * count) != cudaSuccess) {
     set_error("cudaMalloc of a twiddle table failed");
     return DDI_ERR_OOM;
   }
-  p.bytes += es * n;
-  DDI_CUDA(cudaMemcpy(d, host.data(), es * n, cudaMemcpyHostToDevice));
+  p.bytes += es * count;
+  DDI_CUDA(cudaMemcpy(d, host.data(), es * count, cudaMemcpyHostToDevice));
   p.d_tw[b] = d;
   p.tw_n[b] = n;
   return DDI_OK;

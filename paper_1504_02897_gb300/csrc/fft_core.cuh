@@ -34,16 +34,31 @@ __host__ __device__ constexpr double cos16(int k) {
 }
 __host__ __device__ constexpr double sin16(int k) { return cos16(k + 12); }  // sin x = cos(x - pi/2)
 
+// v * k for a constant k known in FP64.  In FP32 the constant is applied as head + tail
+// (k_hi = fl(k), k_lo = fl(k - k_hi)): a single rounded constant would scale every butterfly
+// that uses it by the same |w|^2 != 1 (e.g. 1 - 5.7e-8 for the pi/8 pair), a bias that
+// accumulates over the stages and, in a time-splitting run, drains the mass step after
+// step; with the tail only the unbiased rounding of each operation remains.
+template <typename T>
+__device__ __forceinline__ T mul_const(T v, double k) {
+  if constexpr (sizeof(T) == 4) {
+    const float hi = (float)k;
+    const float lo = (float)(k - (double)hi);
+    return fmaf(v, hi, v * lo);
+  } else {
+    return v * (T)k;
+  }
+}
+
 template <int R, int DIR, typename C>
 __device__ __forceinline__ C tw_const(C x, int k) {
   // x * exp(DIR * 2 pi i k / R) with the trivial factors special-cased
-  using T = decltype(C::x);
   if (k == 0) return x;
   if (4 * k == R) return DIR < 0 ? cmk<C>(x.y, -x.x) : cmk<C>(-x.y, x.x);
   const int idx = (k * (16 / R)) & 15;
-  const T c = (T)cos16(idx);
-  const T s = (T)(DIR * sin16(idx));
-  return cmk<C>(x.x * c - x.y * s, x.x * s + x.y * c);
+  const double c = cos16(idx);
+  const double s = DIR * sin16(idx);
+  return cmk<C>(mul_const(x.x, c) - mul_const(x.y, s), mul_const(x.x, s) + mul_const(x.y, c));
 }
 
 // In-register R-point DFT (natural order in and out), radix-2 decimation in time.
@@ -75,11 +90,11 @@ struct Dft<3, DIR, C> {
   // X1,2 = a - (b + c)/2 +- i DIR (sqrt(3)/2) (b - c)
   __device__ __forceinline__ static void run(C* v) {
     using T = decltype(C::x);
-    const T s3 = (T)0.8660254037844386467637231707529361834714;
+    const double s3 = 0.8660254037844386467637231707529361834714;
     const C t1 = cadd(v[1], v[2]);
     const C d = csub(v[1], v[2]);
     const C t2 = cmk<C>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
-    const C rot = cmk<C>(-(T)DIR * s3 * d.y, (T)DIR * s3 * d.x);
+    const C rot = cmk<C>(-(T)DIR * mul_const(d.y, s3), (T)DIR * mul_const(d.x, s3));
     v[0] = cadd(v[0], t1);
     v[1] = cadd(t2, rot);
     v[2] = csub(t2, rot);
@@ -104,7 +119,9 @@ struct Shape {
 
 // One Stockham stage of radix R with sub-transform length NS; each thread owns
 // G = ceil(RM / R) butterflies of its line (the last ones masked when R does not divide RM).
-template <typename C, int N, int R, int NS, int DIR>
+// PRECISE: apply the twiddle table's tails (FP32), for transforms repeated many times on
+// the same data (time splitting), where a rounded twiddle's |w| != 1 would accumulate
+template <typename C, int N, int R, int NS, int DIR, bool PRECISE>
 __device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) {
   constexpr int RM = Shape<N>::RM;
   constexpr int TPL = Shape<N>::TPL;
@@ -122,9 +139,19 @@ __device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) 
         constexpr int STRIDE = N / (NS * R);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          C w = tw[jm * r * STRIDE];
+          const int ti = jm * r * STRIDE;
+          C w = tw[ti];
           if (DIR > 0) w.y = -w.y;
-          v[g][r] = cmul(v[g][r], w);
+          if constexpr (PRECISE && sizeof(w.x) == 4) {
+            // head + tail twiddle (the table holds N heads, then N tails)
+            C wl = tw[N + ti];
+            if (DIR > 0) wl.y = -wl.y;
+            const C x = v[g][r];
+            v[g][r] = cmk<C>(fmaf(x.x, w.x, fmaf(-x.y, w.y, x.x * wl.x - x.y * wl.y)),
+                             fmaf(x.x, w.y, fmaf(x.y, w.x, x.x * wl.y + x.y * wl.x)));
+          } else {
+            v[g][r] = cmul(v[g][r], w);
+          }
         }
       }
       Dft<R, DIR, C>::run(v[g]);
@@ -144,16 +171,16 @@ __device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) 
   __syncthreads();
 }
 
-template <typename C, int N, int DIR, int NS>
+template <typename C, int N, int DIR, int NS, bool PRECISE>
 struct Stages {
   __device__ __forceinline__ static void run(C* line, int t, const C* tw) {
     constexpr int R = radix_for(N, NS);
-    stage<C, N, R, NS, DIR>(line, t, tw);
-    Stages<C, N, DIR, NS * R>::run(line, t, tw);
+    stage<C, N, R, NS, DIR, PRECISE>(line, t, tw);
+    Stages<C, N, DIR, NS * R, PRECISE>::run(line, t, tw);
   }
 };
-template <typename C, int N, int DIR>
-struct Stages<C, N, DIR, N> {
+template <typename C, int N, int DIR, bool PRECISE>
+struct Stages<C, N, DIR, N, PRECISE> {
   __device__ __forceinline__ static void run(C*, int, const C*) {}
 };
 
@@ -175,8 +202,8 @@ __device__ __forceinline__ long long line_off(const LineGeom& g, long long L) {
 }
 
 // Generic batched-line FFT: a policy P supplies nlines(), contig() (element index fastest
-// in memory), ref(L) (the line's addresses, computed once per line by one thread) and
-// load(ref, i) / store(ref, i, v) for element i of the line.
+// in memory), ref(L) (the line's addresses, computed once per line by one thread),
+// load(ref, i) / store(ref, i, v) for element i of the line and kPreciseTwiddles.
 template <typename T, int N, int LPB, int DIR, typename P>
 __global__ void __launch_bounds__(LPB * Shape<N>::TPL)
     k_fft_policy(P pol, const cx_t<T>* __restrict__ tw) {
@@ -223,7 +250,7 @@ __global__ void __launch_bounds__(LPB * Shape<N>::TPL)
     }
   }
   __syncthreads();
-  Stages<C, N, DIR, 1>::run(sm + (threadIdx.x / TPL) * LS, threadIdx.x % TPL, tw);
+  Stages<C, N, DIR, 1, P::kPreciseTwiddles>::run(sm + (threadIdx.x / TPL) * LS, threadIdx.x % TPL, tw);
   {
     C v[EPT];
 #pragma unroll

@@ -10,6 +10,8 @@
 //            y: only the planes z in the block; only the y in the block are stored;
 //            x: only the rows in the block; the x in the block are stored as
 //               Re(u) / psihat into phi (crop, deconvolution and real part fused).
+// The NUFFT passes run once per evaluation and use the twiddles' FP32 heads only (the
+// path's error budget is 1e-6); the GPE's repeated transforms use heads and tails.
 // Grid positions that are not read are never written in the same evaluation, so no
 // zero-fill of the fine grid is needed.  Each CTA reads its own lines before it writes
 // them and no other CTA touches them, so the in-place passes may load through the
@@ -55,6 +57,7 @@ template <typename T>
 struct PadX {
   using C = cx_t<T>;
   using Ref = RowRef<T>;
+  static constexpr bool kPreciseTwiddles = false;
   Geo<T> g;
   const T* rho;
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }
@@ -75,6 +78,7 @@ struct PadX {
 template <typename T, bool FWD>
 struct BlockY {
   using C = cx_t<T>;
+  static constexpr bool kPreciseTwiddles = false;
   using Ref = long long;  // fine-grid offset of the line's first element
   Geo<T> g;
   __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.az.n; }
@@ -96,6 +100,7 @@ struct BlockY {
 template <typename T, bool FWD>
 struct AllZ {
   using C = cx_t<T>;
+  static constexpr bool kPreciseTwiddles = false;
   using Ref = long long;  // the column's (y, x) offset
   Geo<T> g;
   __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.ay.nf; }
@@ -116,6 +121,7 @@ template <typename T>
 struct CropX {
   using C = cx_t<T>;
   using Ref = RowRef<T>;
+  static constexpr bool kPreciseTwiddles = false;
   Geo<T> g;
   T* phi;
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }

@@ -44,10 +44,23 @@ __device__ __forceinline__ void idx3(long long idx, const G3& g, int& x, int& y,
   z = (int)(r / g.n[1]);
 }
 
-__device__ __forceinline__ void sincos_t(float a, float* s, float* c) { sincosf(a, s, c); }
-__device__ __forceinline__ void sincos_t(double a, double* s, double* c) { sincos(a, s, c); }
+// e^{ia} - 1 = (-2 sin^2(a/2), sin a), accurate also when a is small.  A phase factor is
+// applied as v + v (e^{ia} - 1): in FP32 a rounded e^{ia} near 1 cannot have |e| = 1 (the
+// grid below 1 is 6e-8 apart), and a fixed |e| != 1 per mode or grid point would change
+// the mass by the same amount every step; applied this way only the unbiased rounding
+// of the result remains.
+template <typename T>
+__device__ __forceinline__ cx_t<T> expm1_i(T a) {
+  T s, c;
+  if constexpr (sizeof(T) == 4) {
+    sincosf(0.5f * a, &s, &c);
+  } else {
+    sincos(0.5 * a, &s, &c);
+  }
+  return cmk<cx_t<T>>((T)-2 * s * s, (T)2 * s * c);
+}
 
-// per-axis factors e^{i f mu_d^2} (FP64 built, rounded once) for separable kinetic phases
+// per-axis factors e^{i f mu_d^2} - 1 (FP64 built, rounded once) for separable kinetic phases
 template <typename T>
 __global__ void k_phase_tables(cx_t<T>* tab, G3 g, double f) {
   const int total = g.n[0] + g.n[1] + g.n[2];
@@ -59,22 +72,27 @@ __global__ void k_phase_tables(cx_t<T>* tab, G3 g, double f) {
     }
     const double mu = g.n[d] == 1 ? 0.0 : mode_mu(l, g.n[d], g.len[d]);
     double s, c;
-    sincos(f * mu * mu, &s, &c);
-    tab[i] = cmk<cx_t<T>>((T)c, (T)s);
+    sincos(0.5 * f * mu * mu, &s, &c);
+    tab[i] = cmk<cx_t<T>>((T)(-2.0 * s * s), (T)(2.0 * s * c));
   }
 }
 
-// |e| = 1 restored after the product of the three rounded per-axis factors (FP32): a
-// fixed per-mode |e| != 1 would otherwise change the mass by the same amount every step
-__device__ __forceinline__ float2 unit_phase(float2 e) {
-  const float r = rsqrtf(e.x * e.x + e.y * e.y);
-  return make_float2(e.x * r, e.y * r);
-}
-__device__ __forceinline__ double2 unit_phase(double2 e) { return e; }
-
-// psihat <- psihat * e^{i f |mu|^2} / N_tot using the per-axis tables
+// v * k for a constant known in FP64: head + tail in FP32 (a rounded 1/N would scale the
+// state by the same wrong factor every step)
 template <typename T>
-__global__ void k_kinetic(cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ tab, G3 g, T inv_n) {
+__device__ __forceinline__ T scale_const(T v, double k) {
+  if constexpr (sizeof(T) == 4) {
+    const float hi = (float)k;
+    return fmaf(v, hi, v * (float)(k - (double)hi));
+  } else {
+    return v * (T)k;
+  }
+}
+
+// psihat <- psihat * e^{i f |mu|^2} / N_tot using the per-axis tables of e - 1:
+// (1+A)(1+B)(1+C) - 1 = P + C + C P with P = A + B + A B
+template <typename T>
+__global__ void k_kinetic(cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ tab, G3 g, double inv_n) {
   using C = cx_t<T>;
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
   const C* tx = tab;
@@ -84,8 +102,12 @@ __global__ void k_kinetic(cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ t
        i += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
     idx3(i, g, x, y, z);
-    const C f = unit_phase(cmul(cmul(tx[x], ty[y]), tz[z]));
-    a[i] = cscale(cmul(a[i], f), inv_n);
+    const C A = tx[x], B = ty[y], Cz = tz[z];
+    const C P = cadd(cadd(A, B), cmul(A, B));
+    const C E = cadd(cadd(P, Cz), cmul(Cz, P));
+    const C v = a[i];
+    const C r = cadd(v, cmul(v, E));
+    a[i] = cmk<C>(scale_const(r.x, inv_n), scale_const(r.y, inv_n));
   }
 }
 
@@ -105,9 +127,8 @@ __global__ void k_nonlinear(cx_t<T>* __restrict__ psi, const T* __restrict__ V, 
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const T th = V[i] + beta * rho[i] + lam * phi[i];
-    T s, c;
-    sincos_t(-dt * th, &s, &c);
-    psi[i] = cmul(psi[i], cmk<cx_t<T>>(c, s));
+    const cx_t<T> v = psi[i];
+    psi[i] = cadd(v, cmul(v, expm1_i(-dt * th)));
   }
 }
 
@@ -276,16 +297,15 @@ __global__ void k_adj_a(const cx_t<T>* __restrict__ psi1, const T* __restrict__ 
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const T th = V[i] + beta * rho[i] + lam * phi[i];
-    T s, c;
-    sincos_t(-dt * th, &s, &c);
-    const C e = cmk<C>(c, s);
-    const C psi2 = cmul(psi1[i], e);
+    const C em1 = expm1_i(-dt * th);  // e - 1, applied as in k_nonlinear
+    const C v = psi1[i];
+    const C psi2 = cadd(v, cmul(v, em1));
     // -i dt psi2 = dt (psi2.y, -psi2.x); Re(conj(u) g) = u.x g.x + u.y g.y
     const C g2 = cot[i];
     const T r = dt * (psi2.y * g2.x - psi2.x * g2.y);
     grad[i] += dv * r;
     rout[i] = r;
-    cot[i] = cmul(cconj(e), g2);
+    cot[i] = cadd(g2, cmul(cconj(em1), g2));
   }
 }
 
@@ -326,7 +346,7 @@ struct Gpe {
     C* tab = static_cast<C*>(p.d_kin);
     k_phase_tables<T><<<4, kThreads, 0, s>>>(tab, g, f);
     DDI_LAUNCH_CHECK();
-    k_kinetic<T><<<blocks_for(N), kThreads, 0, s>>>(a, tab, g, (T)(1.0 / (double)N));
+    k_kinetic<T><<<blocks_for(N), kThreads, 0, s>>>(a, tab, g, 1.0 / (double)N);
     DDI_LAUNCH_CHECK();
     return fft(a, +1);
   }

@@ -72,12 +72,13 @@ def test_tsfp_mass_conservation_fp32_64(D):
     psi = _t(psi0, torch.complex64)
     Vt = _t(V, torch.float32)
     m0 = plan.gpe_energy(psi, Vt, 0.0, 0.0)["mass"]
-    plan.gpe_step(psi, Vt, 207.16, 33.1456, 1e-3, 100)
+    plan.gpe_step(psi, Vt, 207.16, 33.1456, 1e-3, 400)
     m1 = plan.gpe_energy(psi, Vt, 0.0, 0.0)["mass"]
-    # Every sub-step is unitary.  In FP32 the rounded FFT twiddles (radix-16 constants
-    # and tables) have |w|^2 - 1 of about -6e-8, the same in every transform, so each
-    # 3-axis FFT pair scales the norm by up to ~6 * 6e-8: the bound is 4e-7 per step.
-    assert abs(m1 - m0) <= 100 * 4e-7
+    # Every sub-step is unitary (Sec. 4.1).  In FP32 the twiddles are applied to FP64
+    # accuracy (head + tail) and the phase factors as v + v (e - 1), so no rounded factor
+    # with |w| != 1 repeats from step to step: the mass takes only the unbiased rounding
+    # of each operation.  Pin: drift <= 1e-5 over 400 steps.
+    assert abs(m1 - m0) <= 1e-5
 
 
 def test_gradient_flow_steps_match_oracle(D):

@@ -21,6 +21,7 @@ constexpr int kRedMax = 8;  // sums per reduction
 struct G3 {
   int n[3];
   double len[3];
+  double ks[3];  // 2 pi / len: mode p has wavenumber p ks
 };
 
 G3 g3_of(const Plan& p) {
@@ -28,20 +29,23 @@ G3 g3_of(const Plan& p) {
   for (int d = 0; d < 3; ++d) {
     g.n[d] = p.n[d];
     g.len[d] = p.desc.len[d] > 0 ? p.desc.len[d] : 1.0;
+    g.ks[d] = 2.0 * M_PI / g.len[d];
   }
   return g;
 }
 
-__device__ __forceinline__ double mode_mu(int l, int n, double len) {
+__device__ __forceinline__ double mode_mu(int l, int n, double ks) {
   const int pp = l < n / 2 ? l : l - n;
-  return (2.0 * M_PI * (double)pp) / len;
+  return (double)pp * ks;
 }
 
+// grids hold < 2^31 points (at most 512^3 in 3D), so 32-bit index arithmetic suffices
 __device__ __forceinline__ void idx3(long long idx, const G3& g, int& x, int& y, int& z) {
-  x = (int)(idx % g.n[0]);
-  const long long r = idx / g.n[0];
-  y = (int)(r % g.n[1]);
-  z = (int)(r / g.n[1]);
+  const unsigned i = (unsigned)idx, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+  const unsigned r = i / n0;
+  x = (int)(i - r * n0);
+  z = (int)(r / n1);
+  y = (int)(r - (unsigned)z * n1);
 }
 
 // e^{ia} - 1 = (-2 sin^2(a/2), sin a), accurate also when a is small.  A phase factor is
@@ -70,7 +74,7 @@ __global__ void k_phase_tables(cx_t<T>* tab, G3 g, double f) {
       l -= g.n[d];
       ++d;
     }
-    const double mu = g.n[d] == 1 ? 0.0 : mode_mu(l, g.n[d], g.len[d]);
+    const double mu = g.n[d] == 1 ? 0.0 : mode_mu(l, g.n[d], g.ks[d]);
     double s, c;
     sincos(0.5 * f * mu * mu, &s, &c);
     tab[i] = cmk<cx_t<T>>((T)(-2.0 * s * s), (T)(2.0 * s * c));
@@ -196,9 +200,9 @@ __global__ void k_red_kinetic(const cx_t<T>* __restrict__ a, G3 g, double* part)
     int x, y, z;
     idx3(i, g, x, y, z);
     double m2 = 0.0;
-    if (g.n[0] > 1) { const double m = mode_mu(x, g.n[0], g.len[0]); m2 += m * m; }
-    if (g.n[1] > 1) { const double m = mode_mu(y, g.n[1], g.len[1]); m2 += m * m; }
-    if (g.n[2] > 1) { const double m = mode_mu(z, g.n[2], g.len[2]); m2 += m * m; }
+    if (g.n[0] > 1) { const double m = mode_mu(x, g.n[0], g.ks[0]); m2 += m * m; }
+    if (g.n[1] > 1) { const double m = mode_mu(y, g.n[1], g.ks[1]); m2 += m * m; }
+    if (g.n[2] > 1) { const double m = mode_mu(z, g.n[2], g.ks[2]); m2 += m * m; }
     const cx_t<T> c = a[i];
     v[0] += m2 * ((double)c.x * c.x + (double)c.y * c.y);
   }
@@ -224,28 +228,42 @@ __global__ void k_red_wrange(const T* __restrict__ V, const T* __restrict__ rho,
 template <typename T>
 __global__ void k_red_maxdiff(const cx_t<T>* __restrict__ a, const cx_t<T>* __restrict__ b, long long total,
                               double* part) {
-  double v[2] = {0.0, 0.0};
+  // maxima of |a - b|^2 and |a|^2 in the working precision (the caller takes the roots);
+  // a non-finite difference counts as infinite
+  T m[2] = {(T)0, (T)0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const cx_t<T> x = a[i], y = b[i];
-    const double dr = (double)x.x - y.x, di = (double)x.y - y.y;
-    const double d = sqrt(dr * dr + di * di);
-    v[0] = fmax(v[0], isfinite(d) ? d : INFINITY);
-    v[1] = fmax(v[1], sqrt((double)x.x * x.x + (double)x.y * x.y));
+    const T dr = x.x - y.x, di = x.y - y.y;
+    const T d2 = dr * dr + di * di;
+    m[0] = isfinite(d2) ? (d2 > m[0] ? d2 : m[0]) : (T)INFINITY;
+    const T a2 = x.x * x.x + x.y * x.y;
+    m[1] = a2 > m[1] ? a2 : m[1];
   }
+  double v[2] = {(double)m[0], (double)m[1]};
   block_max<2>(v, part + (size_t)blockIdx.x * kRedMax);
 }
 
-__global__ void k_red_final(const double* part, int blocks, int k, int is_max, double* out) {
-  // one thread per quantity, blocks summed in index order
+__global__ void __launch_bounds__(256) k_red_final(const double* part, int blocks, int k, int is_max, double* out) {
+  // 256 threads: thread t folds partials t, t + 256, ... in index order, then a fixed
+  // shared-memory tree combines the threads (deterministic)
+  __shared__ double sh[kRedMax][256];
   const int t = threadIdx.x;
-  if (t >= k) return;
-  double s = is_max ? -INFINITY : 0.0;
-  for (int b = 0; b < blocks; ++b) {
-    const double x = part[(size_t)b * kRedMax + t];
-    s = is_max ? fmax(s, x) : s + x;
+  for (int q = 0; q < k; ++q) {
+    double s = is_max ? -INFINITY : 0.0;
+    for (int b = t; b < blocks; b += 256) {
+      const double x = part[(size_t)b * kRedMax + q];
+      s = is_max ? fmax(s, x) : s + x;
+    }
+    sh[q][t] = s;
   }
-  out[t] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w)
+      for (int q = 0; q < k; ++q) sh[q][t] = is_max ? fmax(sh[q][t], sh[q][t + w]) : sh[q][t] + sh[q][t + w];
+    __syncthreads();
+  }
+  if (t < k) out[t] = sh[t][0];
 }
 
 // GF: rhs = phi/dt + (alpha - W) cur, W = V + beta rho + lambda Phi
@@ -265,16 +283,22 @@ __global__ void k_gf_rhs(const cx_t<T>* __restrict__ phi, const cx_t<T>* __restr
 // GF: divide by (1/dt + alpha + |mu|^2/2) and by N_tot
 template <typename T>
 __global__ void k_gf_solve(cx_t<T>* __restrict__ a, G3 g, double inv_dt_alpha, double inv_n) {
+  // in the working precision: the fixed point's own tolerance is the plan's (1e-7 in FP32)
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  const T ks[3] = {(T)g.ks[0], (T)g.ks[1], (T)g.ks[2]};
+  const T c0 = (T)inv_dt_alpha, sc = (T)inv_n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    idx3(i, g, x, y, z);
-    double m2 = 0.0;
-    if (g.n[0] > 1) { const double m = mode_mu(x, g.n[0], g.len[0]); m2 += m * m; }
-    if (g.n[1] > 1) { const double m = mode_mu(y, g.n[1], g.len[1]); m2 += m * m; }
-    if (g.n[2] > 1) { const double m = mode_mu(z, g.n[2], g.len[2]); m2 += m * m; }
-    const T f = (T)(inv_n / (inv_dt_alpha + 0.5 * m2));
+    int q[3];
+    idx3(i, g, q[0], q[1], q[2]);
+    T m2 = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int pp = q[d] < g.n[d] / 2 ? q[d] : q[d] - g.n[d];
+      const T m = (T)pp * ks[d];
+      m2 += g.n[d] > 1 ? m * m : (T)0;
+    }
+    const T f = sc / (c0 + (T)0.5 * m2);
     a[i] = cscale(a[i], f);
   }
 }
@@ -358,7 +382,7 @@ struct Gpe {
   }
 
   int reduce(int k, int is_max, double* host_out) {
-    k_red_final<<<1, 32, 0, s>>>(p.d_red, p.red_blocks, k, is_max, p.d_red + (size_t)p.red_blocks * kRedMax);
+    k_red_final<<<1, 256, 0, s>>>(p.d_red, p.red_blocks, k, is_max, p.d_red + (size_t)p.red_blocks * kRedMax);
     DDI_LAUNCH_CHECK();
     DDI_CUDA(cudaMemcpyAsync(p.h_red, p.d_red + (size_t)p.red_blocks * kRedMax, sizeof(double) * k,
                              cudaMemcpyDeviceToHost, s));
@@ -422,9 +446,9 @@ struct Gpe {
     k_red_maxdiff<T><<<p.red_blocks, kThreads, 0, s>>>(a, b, N, p.d_red);
     DDI_LAUNCH_CHECK();
     double v[2];
-    DDI_TRY(reduce(2, 1, v));
-    *d = v[0];
-    if (amax) *amax = v[1];
+    DDI_TRY(reduce(2, 1, v));  // maxima of the squares
+    *d = std::sqrt(v[0]);
+    if (amax) *amax = std::sqrt(v[1]);
     return DDI_OK;
   }
 

@@ -153,6 +153,15 @@ int ddi_type1(ddi_plan plan, const void* c, void* phi, void* stream);
 /* Original node index q (0..M-1) of each processed node, host pointer [nodes_used]. */
 int ddi_plan_node_order(ddi_plan plan, int64_t* q);
 
+/* New dipole axes for an existing plan (time-dependent axes n(t), m(t), Eq. dipole-time,
+ * Sec. 3; two axes, Eq. dipmn): rebuilds the node scales 2 h^d W_q for the symbol of
+ * (axis_n, axis_m) in one FP64 pass on the device, with the operations of the plan
+ * builder in the same order, so the plan then computes exactly what a plan created with
+ * these axes computes (bit for bit).  axis_n: host pointer to 3 doubles (unit vector;
+ * 2D: n_perp = (n0, n1), n3 = n2); axis_m: 3 doubles or NULL for m = n.  Asynchronous on
+ * `stream` (later calls on the plan see the new axes); DDI_ERR_ARG for a non-unit axis. */
+int ddi_plan_set_axes(ddi_plan plan, const double* axis_n, const double* axis_m, void* stream);
+
 /* ---- GPE (Secs. 3-4) -------------------------------------------------------------- */
 /* nsteps Strang steps of Eq. tssp2, Case I (f = 0, sigma = 1, fixed axis):
  * psi <- K N K psi with K = F^{-1} exp(-i dt |mu|^2/4) F and

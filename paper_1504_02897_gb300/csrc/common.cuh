@@ -126,6 +126,7 @@ struct Plan {
   void* d_l0 = nullptr;       // ushort4 [Mh]: wrapped first tap (x, y, z)
   void* d_psi = nullptr;      // T [Mh][3][w]: kernel values along x, y, z at the w taps
   void* d_scale = nullptr;    // T [Mh]: 2 h^d W_q
+  double4* d_dirw = nullptr;  // [Mh]: direction and weight without the symbol (ddi_plan_set_axes)
   void* d_c = nullptr;        // cx [Mh]: node values c_q
   void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
@@ -224,6 +225,7 @@ int time_spread(Plan& p, cudaStream_t s, int reps, float* ms);  // best of reps 
 int tune_spread_tile(Plan& p, cudaStream_t s);      // autotuner (batch.cu)
 void destroy_plan(Plan& p);
 void fill_info(const Plan& p, ddi_plan_info* info);
+int set_axes(Plan& p, const double* axis_n, const double* axis_m, cudaStream_t s);  // (plan.cu)
 
 }  // namespace ddi
 

@@ -91,7 +91,7 @@ void choose_tile(Plan& p) {
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_fine,  p.d_partial,
+  void* ptrs[] = {p.d_dirw,   p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_fine,  p.d_partial,
                   p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
                   p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out};
   for (void* q : ptrs)
@@ -265,7 +265,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   }
   p.w = kernel_width(d);
   p.beta = kernel_beta(p.w);
-  build_quadrature(d, &p.quad);
+  build_quadrature(d, &p.quad, /*keep_dirs=*/gpe);
   p.M = p.quad.M;
   choose_tile(p);
   const int dim = d.dim, W = p.w;
@@ -336,6 +336,16 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   DDI_TRY(upload(p, &p.d_l0, l0s, "node taps", stream));
   DDI_TRY(upload_real(p, &p.d_psi, psi, "kernel values", stream, &k1));
   DDI_TRY(upload_real(p, &p.d_scale, scale, "node scales", stream, &k2));
+  std::vector<double4> dirw;
+  if (gpe) {
+    // per processed node, what its weight is rebuilt from for other axes
+    dirw.resize(p.Mh);
+    for (int64_t i = 0; i < p.Mh; ++i) {
+      const double* o = &p.quad.dirw[4 * p.order[i]];
+      dirw[i] = make_double4(o[0], o[1], o[2], o[3]);
+    }
+    DDI_TRY(upload(p, (void**)&p.d_dirw, dirw, "node directions", stream));
+  }
   DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
   DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
   DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
@@ -346,6 +356,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   }
   // the host vectors above die with this frame: finish the uploads first
   DDI_CUDA(cudaStreamSynchronize(stream));
+  std::vector<double>().swap(p.quad.dirw);
   DDI_TRY(build_spread(p, stream));
   if (!gpe) return DDI_OK;
   const size_t N = (size_t)p.grid_points();
@@ -365,6 +376,70 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   DDI_TRY(dev_alloc(p, &p.d_io_in, rs * N, "host io in"));
   DDI_TRY(dev_alloc(p, &p.d_io_out, rs * N, "host io out"));
   p.gpe_ready = true;
+  return DDI_OK;
+}
+
+namespace {
+
+// Node scales 2 h^d W_q for the axes (n, m): the symbol and W in the order of operations
+// of build_quadrature (explicitly rounded FP64 operations, no contraction), so the result
+// is bit-identical to a plan built with these axes.
+template <typename T>
+__global__ void k_set_axes(const double4* __restrict__ dirw, T* __restrict__ scale, long long count, int dim,
+                           double n0, double n1, double n2, double m0, double m1, double m2, double nm,
+                           double divisor, double two_dv) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double4 o = dirw[i];
+  double sym;
+  if (dim == 3) {
+    const double nk = __dadd_rn(__dadd_rn(__dmul_rn(n0, o.x), __dmul_rn(n1, o.y)), __dmul_rn(n2, o.z));
+    const double mk = __dadd_rn(__dadd_rn(__dmul_rn(m0, o.x), __dmul_rn(m1, o.y)), __dmul_rn(m2, o.z));
+    sym = __dsub_rn(__dmul_rn(3.0, __dmul_rn(nk, mk)), nm);
+  } else {
+    const double nk = __dadd_rn(__dmul_rn(n0, o.x), __dmul_rn(n1, o.y));
+    const double mk = __dadd_rn(__dmul_rn(m0, o.x), __dmul_rn(m1, o.y));
+    sym = __dmul_rn(1.5, __dsub_rn(__dmul_rn(nk, mk), __dmul_rn(n2, m2)));
+  }
+  const double W = __ddiv_rn(__dmul_rn(o.w, sym), divisor);
+  scale[i] = (T)__dmul_rn(two_dv, W);
+}
+
+}  // namespace
+
+int set_axes(Plan& p, const double* axis_n, const double* axis_m, cudaStream_t s) {
+  if (!p.d_dirw) {
+    set_error("ddi_plan_set_axes: this plan keeps no node directions");
+    return DDI_ERR_ARG;
+  }
+  ddi_plan_desc d = p.desc;
+  for (int a = 0; a < 3; ++a) {
+    d.axis_n[a] = axis_n[a];
+    d.axis_m[a] = axis_m ? axis_m[a] : 0.0;
+  }
+  ddi_plan_desc nd;
+  std::string err;
+  const int st = normalise_desc(&d, &nd, &err);
+  if (st != DDI_OK) {
+    set_error("ddi_plan_set_axes: %s", err.c_str());
+    return st;
+  }
+  const double* n = nd.axis_n;
+  const double* m = nd.axis_m;
+  const double nm = (n[0] * m[0] + n[1] * m[1]) + n[2] * m[2];
+  const double two_dv = 2.0 * p.dv;
+  const unsigned blocks = (unsigned)((p.Mh + 255) / 256);
+  if (p.prec == DDI_FP64)
+    k_set_axes<double><<<blocks, 256, 0, s>>>(p.d_dirw, static_cast<double*>(p.d_scale), p.Mh, p.dim, n[0], n[1],
+                                              n[2], m[0], m[1], m[2], nm, symbol_divisor(p.dim), two_dv);
+  else
+    k_set_axes<float><<<blocks, 256, 0, s>>>(p.d_dirw, static_cast<float*>(p.d_scale), p.Mh, p.dim, n[0], n[1],
+                                             n[2], m[0], m[1], m[2], nm, symbol_divisor(p.dim), two_dv);
+  DDI_LAUNCH_CHECK();
+  for (int a = 0; a < 3; ++a) {
+    p.desc.axis_n[a] = n[a];
+    p.desc.axis_m[a] = m[a];
+  }
   return DDI_OK;
 }
 
@@ -478,6 +553,14 @@ int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info) {
   }
   ddi::fill_info(plan->p, info);
   return DDI_OK;
+}
+
+int ddi_plan_set_axes(ddi_plan plan, const double* axis_n, const double* axis_m, void* stream) {
+  if (!plan || !axis_n) {
+    ddi::set_error("ddi_plan_set_axes: plan and axis_n must not be NULL");
+    return DDI_ERR_ARG;
+  }
+  return ddi::set_axes(plan->p, axis_n, axis_m, static_cast<cudaStream_t>(stream));
 }
 
 int ddi_plan_node_order(ddi_plan plan, int64_t* q) {

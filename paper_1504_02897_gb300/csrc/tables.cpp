@@ -149,7 +149,9 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
   return DDI_OK;
 }
 
-void build_quadrature(const ddi_plan_desc& d, QuadTables* t) {
+double symbol_divisor(int dim) { return dim == 3 ? (kTwoPi * kTwoPi) * kTwoPi : kTwoPi * kTwoPi; }
+
+void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs) {
   t->dim = d.dim;
   for (int a = 0; a < 3; ++a) {
     t->n[a] = d.n[a];
@@ -190,6 +192,7 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t) {
     t->M = (int64_t)d.nr * d.ntheta * d.nphi;
     t->k.resize(3 * t->M);
     t->W.resize(t->M);
+    if (keep_dirs) t->dirw.resize(4 * t->M);
     int64_t q = 0;
     for (int i = 0; i < d.nr; ++i) {
       for (int j = 0; j < d.ntheta; ++j) {
@@ -204,6 +207,13 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t) {
           const double mk = (m0 * hx + m1 * hy) + m2 * hz;
           const double sym = 3.0 * (nk * mk) - nm;
           t->W[q] = (wgt * sym) / tp3;
+          if (keep_dirs) {
+            double* o = &t->dirw[4 * q];
+            o[0] = hx;
+            o[1] = hy;
+            o[2] = hz;
+            o[3] = wgt;
+          }
         }
       }
     }
@@ -212,6 +222,7 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t) {
     t->M = (int64_t)d.nr * d.nphi;
     t->k.resize(2 * t->M);
     t->W.resize(t->M);
+    if (keep_dirs) t->dirw.resize(4 * t->M);
     int64_t q = 0;
     for (int i = 0; i < d.nr; ++i) {
       const double wgt = (wr[i] * wphi) * (r[i] * r[i]);
@@ -222,6 +233,13 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t) {
         const double mk = m0 * c[m] + m1 * s[m];
         const double sym = 1.5 * (nk * mk - n2 * m2);
         t->W[q] = (wgt * sym) / tp2;
+        if (keep_dirs) {
+          double* o = &t->dirw[4 * q];
+          o[0] = c[m];
+          o[1] = s[m];
+          o[2] = 0.0;
+          o[3] = wgt;
+        }
       }
     }
   }

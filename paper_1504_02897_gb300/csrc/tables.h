@@ -19,6 +19,10 @@ struct QuadTables {
   int64_t M = 0;
   std::vector<double> k;  // [M][dim]
   std::vector<double> W;  // [M]
+  // [M][4], filled on request: what W is built from besides the axes, so that the
+  // weights can be rebuilt for other axes (3D: unit direction hx, hy, hz and the weight
+  // without the symbol; 2D: cos, sin, 0 and that weight)
+  std::vector<double> dirw;
 };
 
 // Validates the descriptor and fills defaults; returns DDI_OK or DDI_ERR_ARG with *err set.
@@ -28,7 +32,9 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
 void gauss_legendre(int n, double* x, double* w);
 
 // Quadrature nodes and DDI weights of Sec. 2.1 (Eq. DDI-Trun1) for a normalised descriptor.
-void build_quadrature(const ddi_plan_desc& d, QuadTables* t);
+void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs = false);
+// (2 pi)^d, the divisor of W in build_quadrature, computed as it is there
+double symbol_divisor(int dim);
 
 // Fine-grid oversampling and kernel width for a normalised descriptor.
 int kernel_width(const ddi_plan_desc& d);

@@ -62,7 +62,7 @@ EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_pla
            "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
            "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc",
            "ddi_batch_create", "ddi_batch_destroy", "ddi_batch_size", "ddi_batch_get_info", "ddi_batch_apply",
-           "ddi_batch_graph_stats"]
+           "ddi_batch_graph_stats", "ddi_plan_set_axes"]
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
@@ -98,6 +98,7 @@ def load():
         "ddi_type2": ([vp, vp, vp, vp], ci),
         "ddi_type1": ([vp, vp, vp, vp], ci),
         "ddi_plan_node_order": ([vp, vp], ci),
+        "ddi_plan_set_axes": ([vp, ctypes.POINTER(cd), ctypes.POINTER(cd), vp], ci),
         "gpe_step": ([vp, vp, vp, cd, cd, cd, ci, vp], ci),
         "gpe_energy": ([vp, vp, vp, cd, cd, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_ground_state": ([vp, vp, vp, cd, cd, cd, cd, ci, cd, ci, ci, ctypes.POINTER(GpeStats), vp], ci),
@@ -188,6 +189,16 @@ class Plan:
         self.info = PlanInfo()
         _check(lib.ddi_plan_get_info(self._h, ctypes.byref(self.info)), "ddi_plan_get_info")
         self.dv = float(np.prod([length[d] / n[d] for d in range(dim)]))
+
+    def set_axes(self, axis_n, axis_m=None, stream=None):
+        """New dipole axes for this plan (ddi_plan_set_axes): the node weights are rebuilt
+        on the device; results equal those of a plan created with these axes."""
+        n = (ctypes.c_double * 3)(*[float(v) for v in axis_n])
+        m = (ctypes.c_double * 3)(*[float(v) for v in axis_m]) if axis_m is not None else None
+        _check(load().ddi_plan_set_axes(self._h, n, m, ctypes.c_void_p(_stream(stream))), "ddi_plan_set_axes")
+        for a in range(3):
+            self.desc.axis_n[a] = float(axis_n[a])
+            self.desc.axis_m[a] = float(axis_m[a]) if axis_m is not None else 0.0
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

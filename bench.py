@@ -175,6 +175,53 @@ def run_reference(args):
 # Algorithmic bytes per launch of each kernel of the FP32 path (n = N^3 grid points,
 # fine grid 2N per axis, complex 8 B): each pass moves the data it must read and write
 # once; the padded / cropped passes touch only the block they need.
+def fp64_path_figures(torch, stream, ms, w):
+    """The FP64 path is bound by FP64 arithmetic on this part: its model FLOPs per DDI
+    (interpolation 4 and spread 5 flops per tap, w^3 taps per processed node, plus the six
+    fine-grid FFT passes at 5 n log2 n each) over its time, beside a probed FP64 peak
+    (cuBLAS DGEMM 4096^3, best of 5)."""
+    mh = N * 64 * 128 // 2
+    taps = mh * w ** 3 * 9
+    nf = 2 * N
+    fft = 6 * 5 * nf ** 3 * math.log2(nf)
+    flops = taps + fft
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(a, b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None or t < best else best
+    peak = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+    del a, b
+    return {"ms_per_ddi": ms, "model_gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
+            "dgemm_probe_tflops": peak, "frac_of_probe": flops / (ms * 1e-3) / 1e12 / peak, "kernel_width": w}
+
+
+def cufft_comparator(torch, stream):
+    """cuFFT (through torch.fft) on the same oversampled grid, full 3D C2C forward and
+    inverse of (2N)^3 complex64, best of 5: a timing comparator only (the path's own
+    six passes are pruned to the padded and cropped blocks and fuse pad/crop/deconvolution)."""
+    x = torch.randn(2 * N, 2 * N, 2 * N, dtype=torch.complex64, device="cuda")
+    torch.fft.ifftn(torch.fft.fftn(x))
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.fft.ifftn(torch.fft.fftn(x))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None or t < best else best
+    del x
+    return {"cufft_fwd_inv_ms": best, "grid": [2 * N] * 3}
+
+
 def kernel_bytes(name, info, real=4):
     cx = 2 * real
     n3 = N ** 3
@@ -265,8 +312,11 @@ def main():
         torch.cuda.synchronize()
         if i > 0:
             t64.append(ev[0].elapsed_time(ev[1]))
+    w64 = plan64.info.width
     del plan64, rho64, phi64
     torch.cuda.empty_cache()
+    fp64 = fp64_path_figures(torch, stream, sum(t64) / len(t64), w64)
+    cufft = cufft_comparator(torch, stream)
 
     for i in range(args.warmup):
         flush.fill_(float(i))
@@ -364,8 +414,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _workload_cfg({"fp32_rel_err_vs_fp64": err32, "fp64_ddi_per_s": 1e3 / (sum(t64) / len(t64)),
+                                     "fp64_path": fp64,
                                      "nufft_points_per_s": value * 2 * N * 64 * 128,
                                      "kernel_width": info.width, "spread_tile": list(info.tile),
+                                     "fft_comparator": dict(cufft, ours_six_pruned_passes_ms=sum(
+                                         avg[k] for k in avg if k.startswith(("pad_", "fft_")))),
                                      "wall_s": wall}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dominant,

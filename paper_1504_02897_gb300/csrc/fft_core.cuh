@@ -120,14 +120,15 @@ struct Shape {
 // One Stockham stage of radix R with sub-transform length NS; each thread owns
 // G = ceil(RM / R) butterflies of its line (the last ones masked when R does not divide RM).
 // PRECISE: apply the twiddle table's tails (FP32), for transforms repeated many times on
-// the same data (time splitting), where a rounded twiddle's |w| != 1 would accumulate
+// the same data (time splitting), where a rounded twiddle's |w| != 1 would accumulate.
+// stage_compute reads the stage's inputs from the line, twiddles and transforms them.
 template <typename C, int N, int R, int NS, int DIR, bool PRECISE>
-__device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) {
+__device__ __forceinline__ void stage_compute(const C* line, int t, const C* __restrict__ tw,
+                                              C (&v)[(Shape<N>::RM + R - 1) / R][R]) {
   constexpr int RM = Shape<N>::RM;
   constexpr int TPL = Shape<N>::TPL;
   constexpr int G = (RM + R - 1) / R;
   constexpr int NB = N / R;  // butterflies per line
-  C v[G][R];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int j = t + g * TPL;  // butterfly index in [0, N/R)
@@ -157,6 +158,17 @@ __device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) 
       Dft<R, DIR, C>::run(v[g]);
     }
   }
+}
+
+// a middle stage: shared memory to shared memory (Stockham output order)
+template <typename C, int N, int R, int NS, int DIR, bool PRECISE>
+__device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) {
+  constexpr int RM = Shape<N>::RM;
+  constexpr int TPL = Shape<N>::TPL;
+  constexpr int G = (RM + R - 1) / R;
+  constexpr int NB = N / R;
+  C v[G][R];
+  stage_compute<C, N, R, NS, DIR, PRECISE>(line, t, tw, v);
   __syncthreads();
 #pragma unroll
   for (int g = 0; g < G; ++g) {
@@ -171,16 +183,22 @@ __device__ __forceinline__ void stage(C* line, int t, const C* __restrict__ tw) 
   __syncthreads();
 }
 
-template <typename C, int N, int DIR, int NS, bool PRECISE>
-struct Stages {
+// sub-transform length before the last stage
+__host__ __device__ constexpr int last_ns(int N, int NS = 1) {
+  return NS * radix_for(N, NS) >= N ? NS : last_ns(N, NS * radix_for(N, NS));
+}
+
+// the middle stages, from sub-transform length NS up to (not including) STOP
+template <typename C, int N, int DIR, int NS, int STOP, bool PRECISE>
+struct MidStages {
   __device__ __forceinline__ static void run(C* line, int t, const C* tw) {
     constexpr int R = radix_for(N, NS);
     stage<C, N, R, NS, DIR, PRECISE>(line, t, tw);
-    Stages<C, N, DIR, NS * R, PRECISE>::run(line, t, tw);
+    MidStages<C, N, DIR, NS * R, STOP, PRECISE>::run(line, t, tw);
   }
 };
-template <typename C, int N, int DIR, bool PRECISE>
-struct Stages<C, N, DIR, N, PRECISE> {
+template <typename C, int N, int DIR, int STOP, bool PRECISE>
+struct MidStages<C, N, DIR, STOP, STOP, PRECISE> {
   __device__ __forceinline__ static void run(C*, int, const C*) {}
 };
 
@@ -204,13 +222,26 @@ __device__ __forceinline__ long long line_off(const LineGeom& g, long long L) {
 // Generic batched-line FFT: a policy P supplies nlines(), contig() (element index fastest
 // in memory), ref(L) (the line's addresses, computed once per line by one thread),
 // load(ref, i) / store(ref, i, v) for element i of the line and kPreciseTwiddles.
+// The first Stockham stage takes its inputs straight from global memory and the last one
+// writes its outputs straight back (both are in natural element order there), so each
+// element crosses shared memory once per middle stage plus once between the first stage
+// and the next.  Threads are (line b, butterfly t) pairs: lines fastest when lines are
+// strided in memory (a warp's accesses then cover adjacent lines), butterflies fastest
+// when lines are contiguous.
 template <typename T, int N, int LPB, int DIR, typename P>
 __global__ void __launch_bounds__(LPB * Shape<N>::TPL)
     k_fft_policy(P pol, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
   using Ref = typename P::Ref;
+  constexpr bool PR = P::kPreciseTwiddles;
   constexpr int LS = Shape<N>::LS;
   constexpr int TPL = Shape<N>::TPL;
+  constexpr int RM = Shape<N>::RM;
+  constexpr int R0 = radix_for(N, 1);
+  static_assert(R0 == RM, "the first stage has one butterfly per thread");
+  constexpr int NSL = last_ns(N);      // the last stage's sub-transform length
+  constexpr int RL = N / NSL;          // and its radix
+  constexpr int GL = (RM + RL - 1) / RL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Ref refs[LPB];
   C* sm = reinterpret_cast<C*>(smem_raw);
@@ -219,51 +250,36 @@ __global__ void __launch_bounds__(LPB * Shape<N>::TPL)
   const int nb = left < LPB ? (int)left : LPB;  // lines of this CTA
   if ((int)threadIdx.x < nb) refs[threadIdx.x] = pol.ref(L0 + threadIdx.x);
   __syncthreads();
-  // each thread moves EPT elements; all its global loads are issued before any shared
-  // store (and all its shared loads before any global store) so that they overlap
-  constexpr int NT = LPB * TPL;
-  constexpr int EPT = LPB * N / NT;
   const bool contig = pol.contig();
-  auto coord = [&](int k, int& b, int& i) {
-    const int idx = (int)threadIdx.x + k * NT;
-    if (contig) {
-      b = idx / N;
-      i = idx % N;
-    } else {
-      i = idx / LPB;
-      b = idx % LPB;
-    }
-  };
-  {
-    C v[EPT];
+  const int b = contig ? (int)threadIdx.x / TPL : (int)threadIdx.x % LPB;
+  const int t = contig ? (int)threadIdx.x % TPL : (int)threadIdx.x / LPB;
+  const bool live = b < nb;
+  C* line = sm + b * LS;
+  // first stage: butterfly t takes elements t + r N/R0 (all loads issued before use)
+  C v0[R0];
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      int b, i;
-      coord(k, b, i);
-      v[k] = b < nb ? pol.load(refs[b], i) : cmk<C>((T)0, (T)0);
-    }
+  for (int r = 0; r < R0; ++r) v0[r] = live ? pol.load(refs[b], t + r * (N / R0)) : cmk<C>((T)0, (T)0);
+  Dft<R0, DIR, C>::run(v0);
+  if constexpr (R0 == N) {
+    // a single stage: outputs in natural order
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      int b, i;
-      coord(k, b, i);
-      sm[b * LS + pidx(i)] = v[k];
-    }
-  }
-  __syncthreads();
-  Stages<C, N, DIR, 1, P::kPreciseTwiddles>::run(sm + (threadIdx.x / TPL) * LS, threadIdx.x % TPL, tw);
-  {
-    C v[EPT];
+    for (int r = 0; r < R0; ++r)
+      if (live) pol.store(refs[b], r, v0[r]);
+  } else {
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      int b, i;
-      coord(k, b, i);
-      v[k] = sm[b * LS + pidx(i)];
-    }
+    for (int r = 0; r < R0; ++r) line[pidx(t * R0 + r)] = v0[r];
+    __syncthreads();
+    MidStages<C, N, DIR, R0, NSL, PR>::run(line, t, tw);
+    // last stage: butterfly j's outputs are elements j + r NSL
+    C v[GL][RL];
+    stage_compute<C, N, RL, NSL, DIR, PR>(line, t, tw, v);
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      int b, i;
-      coord(k, b, i);
-      if (b < nb) pol.store(refs[b], i, v[k]);
+    for (int g = 0; g < GL; ++g) {
+      const int j = t + g * TPL;
+      if (live && (RM % RL == 0 || j < N / RL)) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) pol.store(refs[b], j + r * NSL, v[g][r]);
+      }
     }
   }
 }

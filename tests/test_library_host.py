@@ -100,3 +100,24 @@ def test_descriptor_validation(lib, bad):
         lib.quadrature_tables(desc)
     assert e.value.status == -1
     assert len(str(e.value)) > 20
+
+
+def test_null_arguments_are_rejected_before_any_device_work(lib):
+    # argument checks of the entry points that take handles come before any CUDA call,
+    # so they answer DDI_ERR_ARG (or a documented no-op) on a machine without a GPU
+    import ctypes
+    L = lib.load()
+    n = (ctypes.c_double * 3)(0.0, 0.0, 1.0)
+    assert L.ddi_plan_set_axes(None, n, None, None) == -1
+    assert L.ddi_plan_set_axes(ctypes.c_void_p(1), None, None, None) == -1
+    assert L.ddi_batch_size(None) == 0
+    assert L.ddi_batch_destroy(None) == 0
+    assert L.ddi_batch_apply(None, None, None, None) == -1
+    assert L.ddi_batch_get_info(None, 0, None) == -1
+    assert L.ddi_batch_graph_stats(None, None, None) == -1
+    out = ctypes.c_void_p()
+    desc = lib.make_desc(3, (16, 16, 16), (-1, -1, -1), (2, 2, 2), (0, 0, 1))
+    assert L.ddi_batch_create(None, ctypes.byref(desc), 1, 0, None) == -1
+    assert L.ddi_batch_create(ctypes.byref(out), ctypes.byref(desc), 0, 0, None) == -1
+    assert L.ddi_batch_create(ctypes.byref(out), ctypes.byref(desc), 1, 8, None) == -1  # unknown flag
+    assert b"flags" in L.ddi_last_error()

@@ -59,6 +59,63 @@ def tsfp_step(grid, psi, V, beta, lam, dt, ddi):
     return kinetic_half(grid, psi2, dt)
 
 
+# ---- general nonlinearity and damping (Sec. 5, Eqs. DipGPE1, tssp2, fun1, fun2) ----------
+#
+# i psi_t = [-1/2 Lap + V + beta |psi|^(2 sigma) + lambda Phi - i f(|psi|^2)] psi with
+#   Case I   f = 0
+#   Case II  f = delta                  (linear damping)
+#   Case III f = delta rho^q            (q = 1: two-body, q = 2: three-body loss)
+# and a fixed dipole axis.  On the nonlinear sub-step |psi|^2 = h(phi, tau) obeys
+# d h / d tau = -2 f(h) h, and the sub-step is exact:
+#   psi2 = psi1 exp(-i [dt V + H(phi, dt) + G(phi)]) exp(-F(phi, dt)),  phi = |psi1|^2,
+#   H = beta int_0^dt h^sigma,  F = int_0^dt f(h),  G = lambda U_dip * (int_0^dt h).
+
+def damped_density(phi, tau, damping, delta, q):
+    """h(phi, tau): the density after time tau of d h / d tau = -2 f(h) h."""
+    if damping == 0:
+        return phi
+    if damping == 1:
+        return phi * np.exp(-2.0 * delta * tau)
+    return phi / (1.0 + 2.0 * q * delta * tau * phi ** q) ** (1.0 / q)
+
+
+def step_integrals(phi, dt, beta, sigma, damping, delta=0.0, q=1.0):
+    """(H, F, g) of the nonlinear sub-step in closed form (the paper's Cases I-III), with
+    g = int_0^dt h(phi, tau) d tau, so that G = lambda U_dip * g."""
+    phi = np.asarray(phi, dtype=np.float64)
+    if damping == 0:
+        return beta * phi ** sigma * dt, np.zeros_like(phi), phi * dt
+    if damping == 1:
+        H = beta * phi ** sigma / (2.0 * delta * sigma) * (-np.expm1(-2.0 * delta * sigma * dt))
+        F = np.full_like(phi, delta * dt)
+        g = phi / (2.0 * delta) * (-np.expm1(-2.0 * delta * dt))
+        return H, F, g
+    x = 2.0 * q * delta * dt * phi ** q        # 1 + x = (phi / h(phi, dt))^q
+    L = np.log1p(x)
+    F = L / (2.0 * q)
+    if sigma == q:
+        H = beta / (2.0 * q * delta) * L
+    else:
+        H = beta * phi ** (sigma - q) / (2.0 * delta * (q - sigma)) * np.expm1((1.0 - sigma / q) * L)
+    if q == 1:
+        g = np.log1p(2.0 * delta * dt * phi) / (2.0 * delta)
+    else:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.expm1((1.0 - 1.0 / q) * L) / (2.0 * delta * (q - 1.0) * phi ** (q - 1.0))
+        g = np.where(phi > 0, g, 0.0)
+    return H, F, g
+
+
+def tsfp_step_general(grid, psi, V, beta, lam, dt, ddi, sigma=1.0, damping=0, delta=0.0, q=1.0):
+    """One Strang step of Eq. tssp2 for Eq. DipGPE1 with a fixed dipole axis."""
+    psi1 = kinetic_half(grid, psi, dt)
+    phi = np.abs(psi1) ** 2
+    H, F, g = step_integrals(phi, dt, beta, sigma, damping, delta, q)
+    theta = dt * V + H + lam * ddi(g)
+    psi2 = psi1 * np.exp(-1j * theta) * np.exp(-F)
+    return kinetic_half(grid, psi2, dt)
+
+
 def energies(grid, phi, V, beta, lam, ddi):
     """Energy split of Sec. 3.2: E_kin, E_pot, E_int, E_dip, E, mu, virial I, mass."""
     ax = tuple(range(grid.dim))

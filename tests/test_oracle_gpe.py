@@ -143,3 +143,81 @@ def test_adjoint_matches_finite_differences():
         fd = (jp - jm) / (2 * eps)
         ad = float(np.sum(grad * d))
         assert abs(fd - ad) <= 1e-7 * max(abs(fd), 1e-12) + 1e-13, (fd, ad)
+
+
+# ---- general nonlinearity and damping (Sec. 5): the closed forms of H, F, G -----------------
+
+CASES = [  # (sigma, damping, delta, q): Case I cubic and quintic, Case II, Case III (sigma = q and not)
+    (1.0, 0, 0.0, 1.0), (2.0, 0, 0.0, 1.0), (1.0, 1, 0.3, 1.0), (2.0, 1, 0.7, 1.0),
+    (1.0, 2, 0.4, 1.0), (1.0, 2, 0.4, 2.0), (2.0, 2, 0.25, 1.0), (2.0, 2, 0.25, 2.0), (1.5, 2, 0.5, 3.0),
+]
+
+
+@pytest.mark.parametrize("sigma,damping,delta,q", CASES)
+def test_step_integrals_match_their_definitions(sigma, damping, delta, q):
+    # H = beta int_0^dt h^sigma, F = int_0^dt f(h), g = int_0^dt h with d h / d tau = -2 f(h) h
+    # (Eqs. fun1, fun2): integrate that ODE system numerically and compare the closed forms
+    from scipy.integrate import solve_ivp
+    beta, dt = 3.0, 0.37
+    f = (lambda r: 0.0 * r) if damping == 0 else ((lambda r: delta + 0.0 * r) if damping == 1 else (lambda r: delta * r ** q))
+    for phi in (1e-6, 0.05, 0.8, 2.5):
+        def rhs(_, y):
+            h = y[0]
+            return [-2.0 * f(h) * h, beta * h ** sigma, f(h), h]
+        sol = solve_ivp(rhs, (0.0, dt), [phi, 0.0, 0.0, 0.0], method="DOP853", rtol=1e-13, atol=1e-16)
+        h_end, H_ref, F_ref, g_ref = sol.y[:, -1]
+        H, F, g = gpe.step_integrals(np.array([phi]), dt, beta, sigma, damping, delta, q)
+        assert abs(H[0] - H_ref) <= 1e-10 * max(abs(H_ref), 1e-300)
+        assert abs(F[0] - F_ref) <= 1e-10 * max(abs(F_ref), 1e-12)
+        assert abs(g[0] - g_ref) <= 1e-10 * abs(g_ref)
+        assert abs(gpe.damped_density(phi, dt, damping, delta, q) - h_end) <= 1e-10 * h_end
+
+
+def _small_gpe(N=16, L=5.0):
+    n, lo, ln = synth.box(N, L)
+    grid = gpe.Grid(n, lo, ln)
+    t = qd.plan_tables(3, n, ln, (0.0, 0.0, 1.0))
+    ddi = lambda rho: nudft.ddi(rho, t, n, lo, ln)
+    V = synth.harmonic_trap(n, lo, ln, (1, 1, 2))
+    psi0 = synth.gpe_initial(n, lo, ln, (1, 1, 2), eps=0.05, seed=7)
+    return grid, ddi, V, psi0
+
+
+def test_general_step_case_i_equals_tsfp_step():
+    grid, ddi, V, psi0 = _small_gpe()
+    a = gpe.tsfp_step(grid, psi0, V, 20.0, 8.0, 0.01, ddi)
+    b = gpe.tsfp_step_general(grid, psi0, V, 20.0, 8.0, 0.01, ddi, sigma=1.0, damping=0)
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
+
+
+def test_linear_damping_mass_decays_exactly():
+    # Case II: dN/dt = -2 delta N (Eq. Mass_Disp) and the scheme reproduces it exactly
+    grid, ddi, V, psi0 = _small_gpe()
+    delta, dt = 0.2, 0.01
+    psi = psi0
+    m0 = gpe.mass(grid, psi)
+    for k in range(1, 6):
+        psi = gpe.tsfp_step_general(grid, psi, V, 20.0, 8.0, dt, ddi, sigma=1.0, damping=1, delta=delta)
+        assert abs(gpe.mass(grid, psi) - m0 * math.exp(-2 * delta * k * dt)) <= 1e-12 * m0
+
+
+def test_nonlinear_damping_mass_dissipation_law():
+    # Case III, q = 2 (three-body loss): over one step the mass loss matches
+    # 2 int_0^dt h^d sum f(h) h, i.e. the grid sum of phi - h(phi, dt), to roundoff
+    grid, ddi, V, psi0 = _small_gpe()
+    delta, q, dt = 0.5, 2.0, 0.02
+    psi1 = gpe.kinetic_half(grid, psi0, dt)
+    phi = np.abs(psi1) ** 2
+    psi = gpe.tsfp_step_general(grid, psi0, V, 20.0, 8.0, dt, ddi, sigma=1.0, damping=2, delta=delta, q=q)
+    loss = gpe.mass(grid, psi0) - gpe.mass(grid, psi)
+    expected = grid.dv * float(np.sum(phi - gpe.damped_density(phi, dt, 2, delta, q)))
+    assert abs(loss - expected) <= 1e-12 * gpe.mass(grid, psi0)
+
+
+def test_damping_to_zero_recovers_case_i():
+    grid, ddi, V, psi0 = _small_gpe()
+    a = gpe.tsfp_step_general(grid, psi0, V, 20.0, 8.0, 0.01, ddi, sigma=1.0, damping=0)
+    for damping, q in ((1, 1.0), (2, 1.0), (2, 2.0)):
+        b = gpe.tsfp_step_general(grid, psi0, V, 20.0, 8.0, 0.01, ddi, sigma=1.0, damping=damping,
+                                  delta=1e-9, q=q)
+        assert np.max(np.abs(a - b)) <= 1e-7 * np.max(np.abs(a))

@@ -170,6 +170,27 @@ int ddi_plan_set_axes(ddi_plan plan, const double* axis_n, const double* axis_m,
 int gpe_step(ddi_plan plan, void* psi, const void* V, double beta, double lambda,
              double dt, int nsteps, void* stream);
 
+/* Nonlinearity and damping of Eq. DipGPE1 (Sec. 5): beta |psi|^(2 sigma) and
+ * -i f(|psi|^2) psi with f = 0 (GPE_DAMP_NONE, Case I), f = delta (GPE_DAMP_LINEAR, Case II,
+ * inelastic collisions with the background gas) or f = delta rho^q (GPE_DAMP_POWER, Case III;
+ * q = 1 two-body, q = 2 three-body loss). */
+enum { GPE_DAMP_NONE = 0, GPE_DAMP_LINEAR = 1, GPE_DAMP_POWER = 2 };
+typedef struct {
+  double sigma;  /* > 0: 1 cubic, 2 quintic */
+  int damping;   /* GPE_DAMP_* */
+  double delta;  /* > 0 when damped */
+  double q;      /* > 0, GPE_DAMP_POWER only */
+} gpe_nonlinearity;
+
+/* nsteps Strang steps of Eq. tssp2 for Eq. DipGPE1 with a fixed dipole axis: the nonlinear
+ * sub-step psi2 = psi1 exp(-i [dt V + H + lambda U_dip * g]) exp(-F) is integrated exactly,
+ * with H = beta int_0^dt h^sigma, F = int_0^dt f(h), g = int_0^dt h (Eqs. fun1, fun2;
+ * h(phi, tau) the density under the damping alone) in the closed forms of Cases I-III.
+ * Arguments as gpe_step; nl: host pointer.  The mass decays by Eq. Mass_Disp when damped.
+ * DDI_ERR_ARG for out-of-range parameters. */
+int gpe_step_ex(ddi_plan plan, void* psi, const void* V, double beta, double lambda,
+                const gpe_nonlinearity* nl, double dt, int nsteps, void* stream);
+
 /* Energies of Sec. 3.2 (E_kin spectral, FP64 reductions), mu = E + E_int + E_dip,
  * virial I = 2E_kin - 2E_pot + 3E_int + 3E_dip (Eq. vir_iden), mass.  Synchronises. */
 int gpe_energy(ddi_plan plan, const void* psi, const void* V, double beta, double lambda,

@@ -98,6 +98,12 @@ __host__ __device__ inline int rel_start(int l0, int T0, int nf, int w) {
 // minimum two wavefronts.  (16-byte cells fill the window with one 8-cell row segment.)
 __host__ __device__ inline int spread_row_stride(int TX) { return TX + ((8 - TX % 16) + 16) % 16; }
 
+// a processed node's symbol direction (x, y, z; 2D: cos, sin, 0) and weight without the
+// symbol, FP64, from which its weight is rebuilt for other dipole axes
+struct alignas(16) NodeDir {
+  double x, y, z, w;
+};
+
 // ---- the plan ----------------------------------------------------------------------
 struct Plan {
   ddi_plan_desc desc{};
@@ -126,7 +132,7 @@ struct Plan {
   void* d_l0 = nullptr;       // ushort4 [Mh]: wrapped first tap (x, y, z)
   void* d_psi = nullptr;      // T [Mh][3][w]: kernel values along x, y, z at the w taps
   void* d_scale = nullptr;    // T [Mh]: 2 h^d W_q
-  double4* d_dirw = nullptr;  // [Mh]: direction and weight without the symbol (ddi_plan_set_axes)
+  NodeDir* d_dirw = nullptr;  // [Mh]: direction and weight without the symbol (ddi_plan_set_axes)
   void* d_c = nullptr;        // cx [Mh]: node values c_q
   void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]

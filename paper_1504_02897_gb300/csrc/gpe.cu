@@ -124,6 +124,91 @@ __global__ void k_abs2(const cx_t<T>* __restrict__ psi, T* __restrict__ rho, lon
   }
 }
 
+// ---- general nonlinearity and damping (Sec. 5, Eqs. DipGPE1, tssp2, fun1, fun2) -----------
+// On the nonlinear sub-step |psi|^2 = h(phi, tau) obeys dh/dtau = -2 f(h) h; the step is
+// psi2 = psi1 exp(-i [dt V + H + lambda U_dip * g]) exp(-F) with, for phi = |psi1|^2,
+// H = beta int_0^dt h^sigma, F = int_0^dt f(h), g = int_0^dt h, in closed form for
+// f = 0 (Case I), f = delta (Case II), f = delta rho^q (Case III).
+struct NonlinParams {
+  double sigma, delta, q;
+  int damping;          // 0, 1 (linear), 2 (power)
+  double c2_h, c2_g;    // Case II: (1 - e^{-2 delta sigma dt}) / (2 delta sigma), (1 - e^{-2 delta dt}) / (2 delta)
+};
+
+template <typename T>
+__device__ __forceinline__ T powt(T a, T b) {
+  if constexpr (sizeof(T) == 4) return powf(a, b); else return pow(a, b);
+}
+template <typename T>
+__device__ __forceinline__ T log1pt(T a) {
+  if constexpr (sizeof(T) == 4) return log1pf(a); else return log1p(a);
+}
+template <typename T>
+__device__ __forceinline__ T expm1t(T a) {
+  if constexpr (sizeof(T) == 4) return expm1f(a); else return expm1(a);
+}
+
+// g(phi) = int_0^dt h(phi, tau) d tau, the density whose DDI is G / lambda
+template <typename T>
+__global__ void k_step_density(const cx_t<T>* __restrict__ psi, T* __restrict__ gout, NonlinParams nl, T dt,
+                               long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cx_t<T> v = psi[i];
+    const T phi = v.x * v.x + v.y * v.y;
+    T g;
+    if (nl.damping == 0) {
+      g = dt * phi;
+    } else if (nl.damping == 1) {
+      g = (T)nl.c2_g * phi;
+    } else {
+      const T q = (T)nl.q, delta = (T)nl.delta;
+      const T L = log1pt((T)2 * q * delta * dt * powt(phi, q));
+      if (nl.q == 1.0) {
+        g = L / ((T)2 * delta);
+      } else {
+        g = phi > (T)0 ? expm1t(((T)1 - (T)1 / q) * L) / ((T)2 * delta * (q - (T)1) * powt(phi, q - (T)1)) : (T)0;
+      }
+    }
+    gout[i] = g;
+  }
+}
+
+// psi <- psi exp(-i [dt V + H(phi) + lambda Phi_g]) exp(-F(phi)), phi = |psi|^2
+template <typename T>
+__global__ void k_nonlinear_general(cx_t<T>* __restrict__ psi, const T* __restrict__ V, const T* __restrict__ phig,
+                                    T beta, T lam, T dt, NonlinParams nl, long long total) {
+  using C = cx_t<T>;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C v = psi[i];
+    const T phi = v.x * v.x + v.y * v.y;
+    const T sig = (T)nl.sigma;
+    const T ps = nl.sigma == 1.0 ? phi : powt(phi, sig);
+    T H, F;
+    if (nl.damping == 0) {
+      H = beta * ps * dt;
+      F = (T)0;
+    } else if (nl.damping == 1) {
+      H = beta * ps * (T)nl.c2_h;
+      F = (T)nl.delta * dt;
+    } else {
+      const T q = (T)nl.q, delta = (T)nl.delta;
+      const T L = log1pt((T)2 * q * delta * dt * powt(phi, q));
+      F = L / ((T)2 * q);
+      if (nl.sigma == nl.q) {
+        H = beta * L / ((T)2 * q * delta);
+      } else {
+        H = phi > (T)0 ? beta * powt(phi, sig - q) / ((T)2 * delta * (q - sig)) * expm1t(((T)1 - sig / q) * L) : (T)0;
+      }
+    }
+    const T th = dt * V[i] + H + lam * phig[i];
+    const C r = cadd(v, cmul(v, expm1_i(-th)));
+    const T amp = nl.damping == 0 ? (T)1 : (sizeof(T) == 4 ? (T)expf((float)-F) : (T)exp((double)-F));
+    psi[i] = cmk<C>(r.x * amp, r.y * amp);
+  }
+}
+
 // psi <- psi exp(-i dt (V + beta rho + lambda Phi)), rho = |psi|^2 (Case I of Eq. tssp2)
 template <typename T>
 __global__ void k_nonlinear(cx_t<T>* __restrict__ psi, const T* __restrict__ V, const T* __restrict__ rho,
@@ -471,6 +556,26 @@ struct Gpe {
     return DDI_OK;
   }
 
+  // Eq. tssp2 for Eq. DipGPE1 (general nonlinearity and damping, fixed axis)
+  int step_general(C* psi, const T* V, double beta, double lam, const NonlinParams& nl, double dt, int nsteps) {
+    T* g = static_cast<T*>(p.d_rho);
+    T* phi = static_cast<T*>(p.d_phi);
+    DDI_TRY(kinetic(psi, -0.25 * dt));
+    for (int k = 0; k < nsteps; ++k) {
+      k_step_density<T><<<blocks_for(N), kThreads, 0, s>>>(psi, g, nl, (T)dt, N);
+      DDI_LAUNCH_CHECK();
+      if (lam != 0.0) {
+        DDI_TRY(run_ddi<T>(p, g, phi, s));
+      } else {
+        DDI_CUDA(cudaMemsetAsync(phi, 0, sizeof(T) * N, s));
+      }
+      k_nonlinear_general<T><<<blocks_for(N), kThreads, 0, s>>>(psi, V, phi, (T)beta, (T)lam, (T)dt, nl, N);
+      DDI_LAUNCH_CHECK();
+      DDI_TRY(kinetic(psi, k + 1 < nsteps ? -0.5 * dt : -0.25 * dt));
+    }
+    return DDI_OK;
+  }
+
   int adjoint(const C* psi_in, C* cot, T* grad, const T* V, double beta, double lam, double dt) {
     C* psi1 = static_cast<C*>(p.d_psi1);
     T* rho = static_cast<T*>(p.d_rho);
@@ -622,6 +727,31 @@ int gpe_step(ddi_plan plan, void* psi, const void* V, double beta, double lambda
   }
   Gpe<float> g(plan->p, s);
   return g.step(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, dt, nsteps);
+}
+
+int gpe_step_ex(ddi_plan plan, void* psi, const void* V, double beta, double lambda, const gpe_nonlinearity* nl,
+                double dt, int nsteps, void* stream) {
+  DDI_TRY(ddi::check_gpe(plan, psi, V));
+  if (!nl || nsteps < 0 || !ddi::finite_params({beta, lambda, dt, nl->sigma, nl->delta, nl->q}) ||
+      !(nl->sigma > 0.0) || nl->damping < GPE_DAMP_NONE || nl->damping > GPE_DAMP_POWER ||
+      (nl->damping != GPE_DAMP_NONE && !(nl->delta > 0.0)) || (nl->damping == GPE_DAMP_POWER && !(nl->q > 0.0))) {
+    ddi::set_error("gpe_step_ex: nl must not be NULL, nsteps >= 0, parameters finite, sigma > 0, damping one of "
+                   "GPE_DAMP_*, delta > 0 when damped, q > 0 for GPE_DAMP_POWER");
+    return DDI_ERR_ARG;
+  }
+  if (nsteps == 0) return DDI_OK;
+  ddi::NonlinParams np{nl->sigma, nl->delta, nl->q, nl->damping, 0.0, 0.0};
+  if (nl->damping == GPE_DAMP_LINEAR) {
+    np.c2_h = -std::expm1(-2.0 * nl->delta * nl->sigma * dt) / (2.0 * nl->delta * nl->sigma);
+    np.c2_g = -std::expm1(-2.0 * nl->delta * dt) / (2.0 * nl->delta);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->p.prec == DDI_FP64) {
+    Gpe<double> g(plan->p, s);
+    return g.step_general(static_cast<double2*>(psi), static_cast<const double*>(V), beta, lambda, np, dt, nsteps);
+  }
+  Gpe<float> g(plan->p, s);
+  return g.step_general(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, np, dt, nsteps);
 }
 
 int gpe_energy(ddi_plan plan, const void* psi, const void* V, double beta, double lambda, gpe_stats* out,

@@ -336,13 +336,13 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   DDI_TRY(upload(p, &p.d_l0, l0s, "node taps", stream));
   DDI_TRY(upload_real(p, &p.d_psi, psi, "kernel values", stream, &k1));
   DDI_TRY(upload_real(p, &p.d_scale, scale, "node scales", stream, &k2));
-  std::vector<double4> dirw;
+  std::vector<NodeDir> dirw;
   if (gpe) {
     // per processed node, what its weight is rebuilt from for other axes
     dirw.resize(p.Mh);
     for (int64_t i = 0; i < p.Mh; ++i) {
       const double* o = &p.quad.dirw[4 * p.order[i]];
-      dirw[i] = make_double4(o[0], o[1], o[2], o[3]);
+      dirw[i] = NodeDir{o[0], o[1], o[2], o[3]};
     }
     DDI_TRY(upload(p, (void**)&p.d_dirw, dirw, "node directions", stream));
   }
@@ -385,12 +385,12 @@ namespace {
 // of build_quadrature (explicitly rounded FP64 operations, no contraction), so the result
 // is bit-identical to a plan built with these axes.
 template <typename T>
-__global__ void k_set_axes(const double4* __restrict__ dirw, T* __restrict__ scale, long long count, int dim,
+__global__ void k_set_axes(const NodeDir* __restrict__ dirw, T* __restrict__ scale, long long count, int dim,
                            double n0, double n1, double n2, double m0, double m1, double m2, double nm,
                            double divisor, double two_dv) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const double4 o = dirw[i];
+  const NodeDir o = dirw[i];
   double sym;
   if (dim == 3) {
     const double nk = __dadd_rn(__dadd_rn(__dmul_rn(n0, o.x), __dmul_rn(n1, o.y)), __dmul_rn(n2, o.z));

@@ -48,6 +48,14 @@ class PlanInfo(ctypes.Structure):
                 ("spread_tuned_ms", ctypes.c_double)]
 
 
+class GpeNonlinearity(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("damping", ctypes.c_int), ("delta", ctypes.c_double),
+                ("q", ctypes.c_double)]
+
+
+DAMP_NONE, DAMP_LINEAR, DAMP_POWER = 0, 1, 2
+
+
 class GpeStats(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("mu", ctypes.c_double), ("Ekin", ctypes.c_double),
                 ("Epot", ctypes.c_double), ("Eint", ctypes.c_double), ("Edip", ctypes.c_double),
@@ -62,7 +70,7 @@ EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_pla
            "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
            "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc",
            "ddi_batch_create", "ddi_batch_destroy", "ddi_batch_size", "ddi_batch_get_info", "ddi_batch_apply",
-           "ddi_batch_graph_stats", "ddi_plan_set_axes"]
+           "ddi_batch_graph_stats", "ddi_plan_set_axes", "gpe_step_ex"]
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
@@ -100,6 +108,7 @@ def load():
         "ddi_plan_node_order": ([vp, vp], ci),
         "ddi_plan_set_axes": ([vp, ctypes.POINTER(cd), ctypes.POINTER(cd), vp], ci),
         "gpe_step": ([vp, vp, vp, cd, cd, cd, ci, vp], ci),
+        "gpe_step_ex": ([vp, vp, vp, cd, cd, ctypes.POINTER(GpeNonlinearity), cd, ci, vp], ci),
         "gpe_energy": ([vp, vp, vp, cd, cd, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_ground_state": ([vp, vp, vp, cd, cd, cd, cd, ci, cd, ci, ci, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_step_adjoint": ([vp, vp, vp, vp, vp, cd, cd, cd, vp], ci),
@@ -273,6 +282,16 @@ class Plan:
     def gpe_step(self, psi, V, beta, lam, dt, nsteps=1, stream=None):
         _check(load().gpe_step(self._h, self._req(psi, True), self._req(V), float(beta), float(lam), float(dt),
                                int(nsteps), ctypes.c_void_p(_stream(stream))), "gpe_step")
+        return psi
+
+    def gpe_step_ex(self, psi, V, beta, lam, dt, nsteps=1, sigma=1.0, damping=DAMP_NONE, delta=0.0, q=1.0,
+                    stream=None):
+        """Strang steps for the general GPE of Sec. 5 (beta |psi|^(2 sigma), damping f = 0,
+        delta or delta rho^q), fixed axis; see gpe_step_ex in include/ddi.h."""
+        nl = GpeNonlinearity(float(sigma), int(damping), float(delta), float(q))
+        _check(load().gpe_step_ex(self._h, self._req(psi, True), self._req(V), float(beta), float(lam),
+                                  ctypes.byref(nl), float(dt), int(nsteps), ctypes.c_void_p(_stream(stream))),
+               "gpe_step_ex")
         return psi
 
     def gpe_energy(self, psi, V, beta, lam, stream=None):

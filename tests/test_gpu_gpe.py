@@ -145,3 +145,38 @@ def test_virial_table_ground_state_energies(D, row, rule):
     # I is first order in the state error: ~1e-6 after the energy rule; the paper's rule
     # reaches the printed 1e-10 level (Table virial_dip3d: |I^h| <= 6.7e-10)
     assert abs(st["virial"]) <= (1e-5 if rule == 0 else 1e-8), st["virial"]
+
+
+@pytest.mark.parametrize("sigma,damping,delta,q", [
+    (1.0, 0, 0.0, 1.0), (2.0, 0, 0.0, 1.0), (1.0, 1, 0.3, 1.0), (1.0, 2, 0.4, 1.0), (1.0, 2, 0.4, 2.0),
+    (2.0, 2, 0.25, 1.0),
+])
+def test_general_step_matches_oracle(D, sigma, damping, delta, q):
+    # Sec. 5: cubic/quintic nonlinearity, no / linear / two- and three-body damping, FP64
+    # path against the oracle's closed-form step (itself pinned against Eqs. fun1, fun2)
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    beta, lam, dt, steps = 20.0, 8.0, 0.01, 3
+    ref = psi0
+    for _ in range(steps):
+        ref = ogpe.tsfp_step_general(grid, ref, V, beta, lam, dt, ddi, sigma, damping, delta, q)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=0)
+    psi = _t(psi0, plan.cplx_dtype)
+    plan.gpe_step_ex(psi, _t(V, plan.real_dtype), beta, lam, dt, steps, sigma, damping, delta, q)
+    got = psi.cpu().numpy()
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-12
+
+
+def test_general_step_fp32_three_body_loss(D):
+    import torch
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    beta, lam, dt, steps = 20.0, 8.0, 0.01, 5
+    ref = psi0
+    for _ in range(steps):
+        ref = ogpe.tsfp_step_general(grid, ref, V, beta, lam, dt, ddi, 1.0, 2, 0.5, 2.0)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=1)
+    psi = _t(psi0, torch.complex64)
+    plan.gpe_step_ex(psi, _t(V, torch.float32), beta, lam, dt, steps, 1.0, D.DAMP_POWER, 0.5, 2.0)
+    got = psi.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 2e-5
+    with pytest.raises(D.DDIError):
+        plan.gpe_step_ex(psi, _t(V, torch.float32), beta, lam, dt, 1, 1.0, D.DAMP_LINEAR, 0.0)  # delta must be > 0

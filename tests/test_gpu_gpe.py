@@ -180,3 +180,22 @@ def test_general_step_fp32_three_body_loss(D):
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 2e-5
     with pytest.raises(D.DDIError):
         plan.gpe_step_ex(psi, _t(V, torch.float32), beta, lam, dt, 1, 1.0, D.DAMP_LINEAR, 0.0)  # delta must be > 0
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+def test_tsfp_2d_matches_oracle(D, precision, tol):
+    # 2D dynamics (the paper's 2D TS-NUFFT): polar quadrature, n_perp / n_3 axis, 4 Strang steps
+    n, lo, ln = synth.box(32, 6.0, 2)
+    axis = (math.sin(0.6), 0.0, math.cos(0.6))
+    grid = ogpe.Grid(n, lo, ln)
+    t = qd.plan_tables(2, n, ln, axis)
+    ddi = lambda rho: nudft.ddi(rho, t, n, lo, ln)
+    V = synth.harmonic_trap(n, lo, ln, (1, 1.5))
+    psi0 = synth.gpe_initial(n, lo, ln, (1, 1.5), eps=0.05, seed=2)
+    beta, lam, dt, steps = 15.0, 6.0, 0.01, 4
+    ref = ogpe.tsfp_forward(grid, psi0, V, beta, lam, dt, steps, ddi)
+    plan = D.Plan(2, n, lo, ln, axis, precision=precision)
+    psi = _t(psi0, plan.cplx_dtype)
+    plan.gpe_step(psi, _t(V, plan.real_dtype), beta, lam, dt, steps)
+    got = psi.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= tol

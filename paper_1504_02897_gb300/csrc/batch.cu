@@ -37,10 +37,13 @@ std::map<std::string, TuneResult> g_tune_cache;
 }  // namespace
 
 std::string tune_key_of(const Plan& p) {
+  // kmax h_d only along the plan's own axes (a 2D plan's third axis is a placeholder)
+  double kh[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < p.dim; ++a) kh[a] = p.desc.kmax * p.h[a];
   char buf[320];
   snprintf(buf, sizeof buf, "dev%d dim%d prec%d w%d n%d,%d,%d q%d,%d,%d kh%.12g,%.12g,%.12g chunk%d", p.device,
-           p.dim, p.prec, p.w, p.n[0], p.n[1], p.n[2], p.desc.nr, p.desc.ntheta, p.desc.nphi, p.desc.kmax * p.h[0],
-           p.desc.kmax * p.h[1], p.desc.kmax * p.h[2], p.desc.chunk);
+           p.dim, p.prec, p.w, p.n[0], p.n[1], p.n[2], p.desc.nr, p.desc.ntheta, p.desc.nphi, kh[0], kh[1], kh[2],
+           p.desc.chunk);
   return buf;
 }
 

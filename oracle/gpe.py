@@ -200,7 +200,28 @@ def observable_z2(grid, psi):
     return grid.dv * float(np.sum(z * z * np.abs(psi) ** 2))
 
 
-def tsfp_adjoint(grid, psi0, V, beta, lam, dt, nsteps, ddi, gT=None):
+def tsfp_tangent(grid, psi0, V, beta, lam, dt, nsteps, ddi, dpsi0, dV):
+    """Tangent-linear model of ``nsteps`` TSFP steps: the first-order change of psi_T for a
+    change dpsi0 of psi0 and dV of the trap (same in every step).  One step, with
+    psi1 = K psi, rho = |psi1|^2, theta = V + beta rho + lam A rho, psi2 = psi1 exp(-i dt theta):
+        dpsi1 = K dpsi,  drho = 2 Re(conj(psi1) dpsi1),  dtheta = dV + beta drho + lam A drho,
+        dpsi2 = dpsi1 exp(-i dt theta) - i dt dtheta psi2,  dpsi_out = K dpsi2."""
+    psi, d = psi0, dpsi0
+    for _ in range(nsteps):
+        psi1 = kinetic_half(grid, psi, dt)
+        d1 = kinetic_half(grid, d, dt)
+        rho = np.abs(psi1) ** 2
+        ph = np.exp(-1j * dt * (V + beta * rho + lam * ddi(rho)))
+        psi2 = psi1 * ph
+        drho = 2.0 * np.real(np.conj(psi1) * d1)
+        dtheta = dV + beta * drho + (lam * ddi(drho) if lam != 0.0 else 0.0)
+        d2 = d1 * ph - 1j * dt * dtheta * psi2
+        psi = kinetic_half(grid, psi2, dt)
+        d = kinetic_half(grid, d2, dt)
+    return d
+
+
+def tsfp_adjoint(grid, psi0, V, beta, lam, dt, nsteps, ddi, gT=None, return_cot=False):
     """Gradient dJ/dV_j (plain partial derivatives w.r.t. grid values) of J = <z^2>(psi_T).
 
     Pairing <a, b> = Re h^d sum conj(a) b.  For the nonlinear step
@@ -210,7 +231,7 @@ def tsfp_adjoint(grid, psi0, V, beta, lam, dt, nsteps, ddi, gT=None):
         g1  = exp(+i dt theta) g2 + 2 psi1 (beta r + lam A r)
     and the kinetic half step K has adjoint K* = F^{-1} exp(+i dt |mu|^2/4) F.
     Forward states are recomputed from stored step inputs (all steps stored: oracle).
-    Returns (grad_V, J).
+    Returns (grad_V, J), and with ``return_cot`` also the cotangent of psi0.
     """
     states = [psi0]
     psi = psi0
@@ -236,4 +257,6 @@ def tsfp_adjoint(grid, psi0, V, beta, lam, dt, nsteps, ddi, gT=None):
         s_field = beta * r + (lam * ddi(r) if lam != 0.0 else 0.0)
         g1 = np.conj(ph) * g2 + 2.0 * psi1 * s_field
         g = kinetic_half(grid, g1, dt, sign=+1.0)
+    if return_cot:
+        return grad, J, g
     return grad, J

@@ -221,3 +221,34 @@ def test_damping_to_zero_recovers_case_i():
         b = gpe.tsfp_step_general(grid, psi0, V, 20.0, 8.0, 0.01, ddi, sigma=1.0, damping=damping,
                                   delta=1e-9, q=q)
         assert np.max(np.abs(a - b)) <= 1e-7 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_adjoint_dot_product_identity(nsteps):
+    # <S' d, g> = <d_psi, S'^T g>_psi + sum_j dV_j (S'^T g)_V,j for the tangent-linear model S'
+    # of the time-splitting steps and the hand-written adjoint, to roundoff (pairing
+    # <a, b> = Re h^d sum conj(a) b; the V-part of the adjoint is a plain partial derivative)
+    grid, ddi, V, psi0 = _small_gpe(N=12, L=4.0)
+    beta, lam, dt = 20.0, 8.0, 0.02
+    rng = np.random.default_rng(11)
+    dpsi = rng.standard_normal(grid.shape) + 1j * rng.standard_normal(grid.shape)
+    dV = rng.standard_normal(grid.shape)
+    g = rng.standard_normal(grid.shape) + 1j * rng.standard_normal(grid.shape)
+    dT = gpe.tsfp_tangent(grid, psi0, V, beta, lam, dt, nsteps, ddi, dpsi, dV)
+    lhs = grid.dv * float(np.real(np.sum(np.conj(dT) * g)))
+    gV, _, gpsi = gpe.tsfp_adjoint(grid, psi0, V, beta, lam, dt, nsteps, ddi, gT=g, return_cot=True)
+    rhs = grid.dv * float(np.real(np.sum(np.conj(dpsi) * gpsi))) + float(np.sum(dV * gV))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_tangent_linear_model_matches_finite_differences():
+    # the tangent-linear model against central differences of the steps themselves
+    grid, ddi, V, psi0 = _small_gpe(N=12, L=4.0)
+    beta, lam, dt, nsteps, eps = 20.0, 8.0, 0.02, 2, 1e-6
+    rng = np.random.default_rng(12)
+    dpsi = 0.1 * (rng.standard_normal(grid.shape) + 1j * rng.standard_normal(grid.shape))
+    dV = 0.1 * rng.standard_normal(grid.shape)
+    fwd = lambda s: gpe.tsfp_forward(grid, psi0 + s * dpsi, V + s * dV, beta, lam, dt, nsteps, ddi)
+    fd = (fwd(eps) - fwd(-eps)) / (2 * eps)
+    tl = gpe.tsfp_tangent(grid, psi0, V, beta, lam, dt, nsteps, ddi, dpsi, dV)
+    assert np.max(np.abs(fd - tl)) <= 1e-7 * np.max(np.abs(tl))

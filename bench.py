@@ -105,6 +105,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(seconds, dist=None, device="cpu"):
+    """The slowest rank's time (all ranks get it); without a process group, the local time."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of a weak-scaling run: every rank processed units_per_rank
+    independent units (its own density, seed = rank) and the job took the slowest rank's
+    time."""
+    return units_per_rank * world / seconds
+
+
 def cpu_oracle_rate(target_s=12.0, seed=0, max_nodes=None):
     """FP64 oracle (direct nonuniform DFT) on a bounded node sample; returns DDI/s and detail.
 
@@ -345,12 +362,8 @@ def main():
     clocks = sampler.stop() if sampler else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
-    t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    total_ddi = args.steps * world
-    value = total_ddi / tmax
+    tmax = max_over_ranks(dev_s, dist if world > 1 else None, dev)
+    value = weak_scaling_rate(args.steps, world, tmax)
     ms_per_step = tmax / args.steps * 1e3
 
     # per-kernel CUDA-event times (same stream, L2 flushed before each call)
@@ -396,10 +409,7 @@ def main():
     for i in range(e2e_steps):
         plan.apply_host(host_in, host_out)
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = e2e_steps * world / float(te.item())
+    e2e_value = weak_scaling_rate(e2e_steps, world, max_over_ranks(e2e_s, dist if world > 1 else None, dev))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

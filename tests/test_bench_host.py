@@ -1,0 +1,57 @@
+"""The multi-GPU bookkeeping of bench.py on CPU: two gloo ranks (127.0.0.1), each with its
+own seeded density, agree on the slowest rank's time and the whole-job weak-scaling rate."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1504_02897_gb300 import synth
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        rho = synth.gaussian_mixture_density(16, 4.0, seed=rank)["rho"]   # the rank's own unit of work
+        local = 1.0 + rank                                                  # rank r "took" 1 + r seconds
+        tmax = bench.max_over_ranks(local, dist, "cpu")
+        out.put((rank, tmax, bench.weak_scaling_rate(10, world, tmax), float(rho.sum()), float(rho[8, 8, 8])))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_max_time_and_rate():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, t0, v0, m0, c0), (r1, t1, v1, m1, c1) = res
+    assert (r0, r1) == (0, 1)
+    assert t0 == t1 == 2.0                      # both see the slowest rank
+    assert v0 == v1 == pytest.approx(10 * 2 / 2.0)
+    assert c0 != c1                             # different densities per rank (seed = rank)
+
+
+def test_single_process_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(1.5) == 1.5
+    assert bench.weak_scaling_rate(40, 1, 0.02) == pytest.approx(2000.0)

@@ -14,7 +14,10 @@ nudft         the discrete quadrature sum evaluated as a direct nonuniform DFT
 closed_forms  closed-form dipolar potentials of Gaussian densities
               (Eq. extDensGausDipolar / Hessian_Ex1, the 2D Bessel form of
               Example 2d_exmp, and 1-D integral forms derived from the symbol).
-gpe           TSFP step (Eq. tssp2, Case I), energies (Sec. 3.2), normalised
-              gradient flow with backward Euler (Eqs. gf-eq2..gffg33) and the
-              adjoint of the TSFP step.
+gpe           TSFP step (Eq. tssp2; Case I and the general nonlinearity/damping
+              of Sec. 5), energies (Sec. 3.2), normalised gradient flow with
+              backward Euler (Eqs. gf-eq2..gffg33), the adjoint and the
+              tangent-linear model of the TSFP step.
+split         the improved split algorithm (Eq. 3.9): a padded-FFT convolution
+              with the smooth part of the symbol plus a small-ball quadrature.
 """

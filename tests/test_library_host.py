@@ -121,3 +121,23 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert L.ddi_batch_create(ctypes.byref(out), ctypes.byref(desc), 0, 0, None) == -1
     assert L.ddi_batch_create(ctypes.byref(out), ctypes.byref(desc), 1, 8, None) == -1  # unknown flag
     assert b"flags" in L.ddi_last_error()
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as C99 and links against the library
+    import shutil
+    import subprocess
+    from paper_1504_02897_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "ddi.h"\n#include <string.h>\n'
+                   'int main(void) { ddi_plan_desc d; memset(&d, 0, sizeof d);\n'
+                   '  return strlen(ddi_status_str(DDI_ERR_ARG)) > 0 && ddi_batch_size(0) == 0 ? 0 : 1; }\n')
+    exe = tmp_path / "use"
+    lib = build.LIB
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0

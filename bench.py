@@ -244,7 +244,10 @@ def kernel_bytes(name, info, real=4):
     n3 = N ** 3
     mh = int(info.nodes_used)
     node_in = mh * (8 + 4 * real)          # ushort4 start taps + 4 reals (offsets, weight)
-    ball = int(4.0 / 3.0 * 3.141592653589793 * (N + info.width / 2.0) ** 3) * cx   # cells the taps reach
+    # cells the taps reach: the ball |k| <= kmax is kmax (nf h / 2 pi) = kmax 2L / pi fine cells
+    # in radius (N for the full rule, kmax = pi / h)
+    radius = info.kmax * 2 * L / math.pi
+    ball = int(4.0 / 3.0 * math.pi * (radius + info.width / 2.0) ** 3) * cx
     table = {
         "pad_fft_x": n3 * real + 2 * n3 * cx,           # read rho, write N^2 rows of 2N
         "fft_y_fwd": 2 * n3 * cx + 4 * n3 * cx,         # read the block half, write planes
@@ -255,8 +258,13 @@ def kernel_bytes(name, info, real=4):
         "fft_z_inv": 8 * n3 * cx + 4 * n3 * cx,
         "fft_y_inv": 4 * n3 * cx + 2 * n3 * cx,
         "fft_x_inv_crop": 2 * n3 * cx + n3 * real,
+        "fft_x_inv_crop_add": 2 * n3 * cx + 2 * n3 * real,  # also reads phi (split plans)
     }
-    return table.get(name, 0)
+    # the split algorithm's smooth part: the same passes without the deconvolution
+    smooth = {"smooth_pad_fft_x": "pad_fft_x", "smooth_fft_y_fwd": "fft_y_fwd", "smooth_fft_z_symbol": "fft_z_fwd",
+              "smooth_fft_z_inv": "fft_z_inv", "smooth_fft_y_inv": "fft_y_inv",
+              "smooth_fft_x_inv_crop": "fft_x_inv_crop"}
+    return table.get(smooth.get(name, name), 0)
 
 
 def main():
@@ -266,8 +274,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ddi3d_128", choices=["ddi3d_128", "batch2d_96", "tsfp128", "gs128", "grad128"],
-                    help="ddi3d_128: the headline 3D workload; batch2d_96: 96 2D densities in one batch; "
+    ap.add_argument("--workload", default="ddi3d_128",
+                    choices=["ddi3d_128", "ddi3d_128_split", "batch2d_96", "tsfp128", "gs128", "grad128"],
+                    help="ddi3d_128: the headline 3D workload; ddi3d_128_split: the same density by the "
+                         "improved split algorithm (Eq. 3.9); batch2d_96: 96 2D densities in one batch; "
                          "tsfp128 / gs128 / grad128: the GPE step, ground state and trap gradient at 128^3")
     ap.add_argument("--fp64-check", type=int, default=1, help="grad128: also run the FP64 path for its error")
     args = ap.parse_args()
@@ -277,6 +287,9 @@ def main():
         return
     if args.workload == "batch2d_96":
         bench_batch2d(args)
+        return
+    if args.workload == "ddi3d_128_split":
+        bench_split(args)
         return
     if args.workload in ("tsfp128", "gs128", "grad128"):
         bench_gpe(args)
@@ -445,6 +458,133 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed_steps(torch, stream, flush, steps, fn):
+    """Device time of `steps` calls of fn, each after a 256 MiB L2 flush, with CUDA events on
+    the launching stream; nvidia-smi clocks sampled meanwhile."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3, clocks
+
+
+def bench_split(args):
+    """The improved split algorithm (Sec. 2.1, Eq. 3.9) on the 128^3 mixture density of the
+    headline workload: FP32 plan with the library's default window k0 = 9.6 / 24 = 0.4, ball
+    |k| <= 6 k0 = 2.4 with 48 x 32 x 64 nodes, smooth part by the 2x zero-padded FFT
+    convolution on the fine grid.  Reports DDI/s, the FP32 error against the FP64 split path
+    (itself parity-tested against the oracle), the difference between the split result and
+    the 128 x 64 x 128 spherical rule, per-kernel times and the HBM roofline of the dominant
+    kernel.  One GPU (the workload is one density)."""
+    import numpy as np
+    import torch
+    from paper_1504_02897_gb300 import build, ddi, synth
+
+    torch.cuda.set_device(0)
+    build.build()
+    ddi.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    w = synth.gaussian_mixture_density(N, L, seed=0)
+    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP32, tile=(-1, 0, 0), split_k0=-1.0)
+    rho = torch.from_numpy(w["rho"]).to(dev, torch.float32)
+    phi = torch.empty_like(rho)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    rho64 = torch.from_numpy(w["rho"]).to(dev)
+    p64 = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP64, split_k0=-1.0)
+    phi64 = p64.apply(rho64)
+    del p64
+    full = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=ddi.FP64, **SIZES)
+    phifull = full.apply(rho64)
+    del full
+    plan.apply(rho, phi)
+    torch.cuda.synchronize()
+    err32 = float((phi.double() - phi64).abs().max() / phi64.abs().max())
+    d = (phi64 - phifull).abs()
+    c = torch.arange(N, device=dev)
+    inner = ((c >= N // 4) & (c < 3 * N // 4))
+    m3 = inner[:, None, None] & inner[None, :, None] & inner[None, None, :]
+    diff_rule = float(d.max() / phifull.abs().max())
+    diff_rule_inner = float(d[m3].max() / phifull.abs().max())
+    del phi64, phifull, rho64, d
+    torch.cuda.empty_cache()
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        plan.apply(rho, phi)
+    dev_s, clocks = _timed_steps(torch, stream, flush, args.steps, lambda: plan.apply(rho, phi))
+    value = args.steps / dev_s
+    ms_per_step = dev_s / args.steps * 1e3
+
+    per = {}
+    launches = 0
+    for i in range(8):
+        flush.fill_(float(i))
+        _, marks = plan.apply_timed(rho, phi)
+        launches = len(marks)
+        if i < 2:
+            continue
+        for name, ms in marks:
+            per.setdefault(name, []).append(ms)
+    avg = {k: sum(v) / len(v) for k, v in per.items()}
+    dominant = max(avg, key=avg.get)
+    peaks, src = _peaks()
+    peak = float(peaks["hbm_gbs"])
+    info = plan.info
+    alg = kernel_bytes(dominant, info)
+    achieved = alg / (avg[dominant] * 1e-3) / 1e9
+    # the method's bytes: rho in, phi out and the smooth part's four sweeps of the padded
+    # grid (write after the pad, one FFT pass, read by the crop); the ball's part costs O(1)
+    # in the method but runs through the fine grid here (its six passes are counted apart)
+    method_bytes = 8 * N ** 3 + 4 * (2 * N) ** 3 * 8
+    impl_bytes = method_bytes + 4 * (2 * N) ** 3 * 8
+
+    host_in = torch.from_numpy(w["rho"].astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(2):
+        plan.apply_host(host_in, host_out)
+    e2e_steps = max(5, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.apply_host(host_in, host_out)
+    e2e_value = e2e_steps / (time.perf_counter() - t0)
+
+    out = {
+        "metric": "3D DDI evals/s at 128^3 by the split algorithm (Eq. 3.9; FP32-mixed vs FP64)", "value": value,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ddi3d_128cubed_mixture8_tilt30_split_k0_0.4_ball48x32x64", "grid": [N, N, N],
+                   "box": [-L, L], "split_k0": info.split_k0, "ball_kmax": info.kmax,
+                   "ball_quadrature": [info.nr, info.ntheta, info.nphi], "nodes": int(info.nodes),
+                   "spread_tile": list(info.tile), "fp32_rel_err_vs_fp64": err32,
+                   "split_vs_spherical_rule_rel_diff": diff_rule,
+                   "split_vs_spherical_rule_rel_diff_inner_half_box": diff_rule_inner,
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": dominant, "kernel_ms": avg[dominant],
+                     "peak_source": src + " hbm_gbs (copy)"},
+        "ddi_roofline": {"method_bytes": method_bytes, "implementation_bytes": impl_bytes,
+                         "frac_of_method": method_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+                         "frac_of_implementation": impl_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+        "kernel_ms": avg,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N ** 3, "d2h_bytes_per_step": 4 * N ** 3},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
 
 
 def bench_batch2d(args):

@@ -71,6 +71,20 @@ typedef struct {
                           such a size); 0 => built-in choice; tile[0] < 0 => picked by the
                           spread-tile autotuner (ddi_tune_spread_tile) when the plan is created */
   int chunk;           /* max nodes per spread work item; 0 => built-in choice */
+  double split_k0;     /* 3D only.  0 => the quadrature of Eq. DDI-Trun1 on the ball |k| <= kmax.
+                          != 0 => the improved split algorithm of Sec. 2.1 (Eq. 3.9) with the window
+                          q(k) = exp(-|k|^2 / k0^2), k0 = split_k0 (< 0 => k0 = 9.6 / min_d len_d: the
+                          smooth part's kernel decays like exp(-(k0 r)^2 / 4), ~1e-10 at the distance
+                          len_d that the 2x zero padding puts between a point and the nearest
+                          periodic image of the box):
+                            Phi = I_1 + I_2,
+                            I_1 = Re IFFT[ p(k_l) FFT[rho zero-padded to the 2n fine grid] ], cropped,
+                                  p = (1 - q) Uhat, on the fine grid's modes k_l = 2 pi l / (2 len);
+                            I_2 = the quadrature sum of Eq. DDI-Trun1 on the small ball
+                                  |k| <= kmax (0 => 6 k0) with weights W_q q(k_q), by the NUFFT.
+                          Quadrature sizes 0 => nr = 0.48 K, ntheta = 0.32 K, nphi = 0.64 K, each
+                          rounded up to a multiple of 8 and at least (16, 8, 16), K = kmax times the
+                          box diagonal (the phase range of e^{ik.x} the ball rule has to resolve). */
 } ddi_plan_desc;
 
 /* Read-only facts about a built plan (sizes and the NUFFT parameters chosen). */
@@ -88,6 +102,7 @@ typedef struct {
   int nr, ntheta, nphi;
   size_t device_bytes; /* device memory held by the plan */
   double spread_tuned_ms; /* spread time of the tile the autotuner picked, in ms; 0 if not tuned */
+  double split_k0;     /* window width k0 of the split algorithm; 0 if the plan does not split */
 } ddi_plan_info;
 
 /* Energies of Sec. 3.2 for a state phi (all FP64). */

@@ -135,6 +135,7 @@ struct Plan {
   NodeDir* d_dirw = nullptr;  // [Mh]: direction and weight without the symbol (ddi_plan_set_axes)
   void* d_c = nullptr;        // cx [Mh]: node values c_q
   void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
+  void* d_ones = nullptr;     // T [n0 + n1 + n2] of ones: the pad and crop of a split plan's smooth part
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
   void* d_partial = nullptr;  // cx [nslots * tile cells]
   int4* d_visits = nullptr;   // spread visit lists: (node, ox, oy, oz) relative to the tile
@@ -176,6 +177,9 @@ struct Plan {
     ++nmarks;
   }
 
+  // the improved split algorithm (Eq. 3.9): the nodes are the small ball's, and the smooth
+  // part is added by a padded FFT convolution
+  bool split() const { return desc.split_k0 > 0.0; }
   int64_t grid_points() const { return (int64_t)n[0] * n[1] * n[2]; }
   // cells of one owned plane's shared-memory buffer (padded row stride)
   size_t spread_plane_cells() const { return (size_t)tile[1] * spread_row_stride(tile[0]); }
@@ -201,7 +205,11 @@ int make_twiddles(Plan& p, int n);
 
 // ---- pruned / fused fine-grid FFTs of the NUFFT (fft_nufft.cu) ----------------------
 template <typename T> int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t s);  // rho -> F (fine grid)
-template <typename T> int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s);        // U (fine grid) -> phi
+// U (fine grid) -> phi; acc: phi += the result instead of phi = the result
+template <typename T> int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s, bool acc = false);
+// split plans: phi = I_1 of Eq. 3.9 (zero-padded FFT convolution of rho with the smooth
+// symbol p = (1 - q) Uhat on the fine grid); reads rho before it writes phi (they may alias)
+template <typename T> int split_smooth_part(Plan& p, const T* rho, T* phi, cudaStream_t s);
 
 // ---- NUFFT stages (nufft.cu) --------------------------------------------------------
 template <typename T> int run_type2(Plan& p, const T* rho, cudaStream_t s);         // rho -> d_c

@@ -12,6 +12,8 @@
 //               Re(u) / psihat into phi (crop, deconvolution and real part fused).
 // The NUFFT passes run once per evaluation and use the twiddles' FP32 heads only (the
 // path's error budget is 1e-6); the GPE's repeated transforms use heads and tails.
+// Split plans (Eq. 3.9) run the same six passes a second time for the smooth part I_1,
+// without the deconvolution and with the symbol p applied as the forward z pass stores.
 // Grid positions that are not read are never written in the same evaluation, so no
 // zero-fill of the fine grid is needed.  Each CTA reads its own lines before it writes
 // them and no other CTA touches them, so the in-place passes may load through the
@@ -116,8 +118,9 @@ struct AllZ {
   }
 };
 
-// inverse x with crop, deconvolution and real part: lines = grid rows (jy, jz)
-template <typename T>
+// inverse x with crop, deconvolution and real part: lines = grid rows (jy, jz); ACC adds
+// the result to phi instead of storing it
+template <typename T, bool ACC>
 struct CropX {
   using C = cx_t<T>;
   using Ref = RowRef<T>;
@@ -134,17 +137,82 @@ struct CropX {
   __device__ void store(const Ref& r, int i, C v) const {
     if (!g.ax.in_block(i)) return;
     const int jx = g.ax.grid_of(i);
-    phi[r.grid + jx] = v.x * (g.dcx[jx] * r.dy * r.dz);
+    const T val = v.x * (g.dcx[jx] * r.dy * r.dz);
+    if (ACC)
+      phi[r.grid + jx] += val;
+    else
+      phi[r.grid + jx] = val;
   }
 };
 
+// The smooth symbol of the split algorithm (Eq. 3.9) at the fine grid's modes,
+//   p(k) = (1 - e^{-|k|^2/k0^2}) / |k|^2 * (3 (n.k)(m.k) - (n.m) |k|^2),  p(0) = 0,
+// times the inverse transform's 1 / (nf0 nf1 nf2).  Mode l of an axis with nf points is the
+// wavenumber (2 pi / (nf h)) l~ with l~ = l for l < nf/2, else l - nf.
 template <typename T>
-Geo<T> geo_of(Plan& p) {
+struct SmoothSymbol {
+  T dk[3];    // 2 pi / (nf_d h_d)
+  T n[3], m[3];
+  T nm;       // n.m
+  T inv_k02;  // 1 / k0^2
+  T scale;    // 1 / (nf0 nf1 nf2)
+  __host__ __device__ T k_of(int a, int l, int nf) const { return dk[a] * (T)(l < nf / 2 ? l : l - nf); }
+  __device__ T operator()(T kx, T ky, T kz) const {
+    const T k2 = (kx * kx + ky * ky) + kz * kz;
+    const T nk = (n[0] * kx + n[1] * ky) + n[2] * kz;
+    const T mk = (m[0] * kx + m[1] * ky) + m[2] * kz;
+    const T poly = (T)3 * (nk * mk) - nm * k2;
+    T f;
+    if (k2 > (T)0) {
+      if constexpr (sizeof(T) == 4)
+        f = -expm1f(-(k2 * inv_k02)) / k2;
+      else
+        f = -expm1(-(k2 * inv_k02)) / k2;
+    } else {
+      f = inv_k02;
+    }
+    return (f * poly) * scale;
+  }
+};
+
+// forward z of the split algorithm's smooth part, with the symbol applied as the
+// transformed column is stored: lines = columns (ly, lx) of the fine grid
+template <typename T>
+struct ZRef {
+  long long col;  // the column's (y, x) offset
+  T kx, ky;       // the column's x and y wavenumbers
+};
+
+template <typename T>
+struct SmoothZ {
+  using C = cx_t<T>;
+  using Ref = ZRef<T>;
+  static constexpr bool kPreciseTwiddles = false;
+  Geo<T> g;
+  SmoothSymbol<T> sy;
+  __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.ay.nf; }
+  __device__ bool contig() const { return false; }
+  __device__ Ref ref(long long L) const {
+    const int lx = (int)(L % g.ax.nf), ly = (int)(L / g.ax.nf);
+    return Ref{L, sy.k_of(0, lx, g.ax.nf), sy.k_of(1, ly, g.ay.nf)};
+  }
+  __device__ C load(const Ref& r, int i) const {
+    if (!g.az.in_block(i)) return cmk<C>((T)0, (T)0);
+    return __ldg(g.fine + (long long)i * g.ay.nf * g.ax.nf + r.col);
+  }
+  __device__ void store(const Ref& r, int i, C v) const {
+    g.fine[(long long)i * g.ay.nf * g.ax.nf + r.col] = cscale(v, sy(r.kx, r.ky, sy.k_of(2, i, g.az.nf)));
+  }
+};
+
+// unit: the pad and crop without the deconvolution (the split algorithm's smooth part)
+template <typename T>
+Geo<T> geo_of(Plan& p, bool unit = false) {
   Geo<T> g;
   g.ax = Axis{p.n[0], p.nf[0]};
   g.ay = Axis{p.n[1], p.nf[1]};
   g.az = Axis{p.n[2], p.nf[2]};
-  const T* dc = static_cast<const T*>(p.d_deconv);
+  const T* dc = static_cast<const T*>(unit ? p.d_ones : p.d_deconv);
   g.dcx = dc;
   g.dcy = dc + p.n[0];
   g.dcz = dc + p.n[0] + p.n[1];
@@ -169,7 +237,7 @@ int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t s) {
 }
 
 template <typename T>
-int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s) {
+int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s, bool acc) {
   const Geo<T> g = geo_of<T>(p);
   if (p.dim == 3) {
     DDI_TRY((dispatch_policy<T, +1>(p.nf[2], AllZ<T, false>{g}, twiddles(p, p.nf[2]), s)));
@@ -177,14 +245,56 @@ int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s) {
   }
   DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BlockY<T, false>{g}, twiddles(p, p.nf[1]), s)));
   p.mark("fft_y_inv", s);
-  DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T>{g, phi}, twiddles(p, p.nf[0]), s)));
-  p.mark("fft_x_inv_crop", s);
+  if (acc)
+    DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T, true>{g, phi}, twiddles(p, p.nf[0]), s)));
+  else
+    DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T, false>{g, phi}, twiddles(p, p.nf[0]), s)));
+  p.mark(acc ? "fft_x_inv_crop_add" : "fft_x_inv_crop", s);
+  return DDI_OK;
+}
+
+// I_1 of Eq. 3.9: rho zero-padded into the fine grid (the centred block, as for the NUFFT,
+// which leaves the circular convolution unchanged), forward x, y, z with p applied as z is
+// stored, inverse z, y, x, crop and real part.  The 2x padding makes the circular
+// convolution linear up to the kernel's tail beyond one box length.
+template <typename T>
+int split_smooth_part(Plan& p, const T* rho, T* phi, cudaStream_t s) {
+  if (p.dim != 3 || !p.split() || !p.d_ones) {
+    set_error("split_smooth_part: not a 3D split plan");
+    return DDI_ERR_ARG;
+  }
+  const Geo<T> g = geo_of<T>(p, /*unit=*/true);
+  SmoothSymbol<T> sy;
+  for (int a = 0; a < 3; ++a) {
+    sy.dk[a] = (T)((2.0 * M_PI) / ((double)p.nf[a] * p.h[a]));
+    sy.n[a] = (T)p.desc.axis_n[a];
+    sy.m[a] = (T)p.desc.axis_m[a];
+  }
+  const double* n = p.desc.axis_n;
+  const double* m = p.desc.axis_m;
+  sy.nm = (T)((n[0] * m[0] + n[1] * m[1]) + n[2] * m[2]);
+  sy.inv_k02 = (T)(1.0 / (p.desc.split_k0 * p.desc.split_k0));
+  sy.scale = (T)(1.0 / ((double)p.nf[0] * (double)p.nf[1] * (double)p.nf[2]));
+  DDI_TRY((dispatch_policy<T, -1>(p.nf[0], PadX<T>{g, rho}, twiddles(p, p.nf[0]), s)));
+  p.mark("smooth_pad_fft_x", s);
+  DDI_TRY((dispatch_policy<T, -1>(p.nf[1], BlockY<T, true>{g}, twiddles(p, p.nf[1]), s)));
+  p.mark("smooth_fft_y_fwd", s);
+  DDI_TRY((dispatch_policy<T, -1>(p.nf[2], SmoothZ<T>{g, sy}, twiddles(p, p.nf[2]), s)));
+  p.mark("smooth_fft_z_symbol", s);
+  DDI_TRY((dispatch_policy<T, +1>(p.nf[2], AllZ<T, false>{g}, twiddles(p, p.nf[2]), s)));
+  p.mark("smooth_fft_z_inv", s);
+  DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BlockY<T, false>{g}, twiddles(p, p.nf[1]), s)));
+  p.mark("smooth_fft_y_inv", s);
+  DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T, false>{g, phi}, twiddles(p, p.nf[0]), s)));
+  p.mark("smooth_fft_x_inv_crop", s);
   return DDI_OK;
 }
 
 template int nufft_forward_fft<float>(Plan&, const float*, cudaStream_t);
 template int nufft_forward_fft<double>(Plan&, const double*, cudaStream_t);
-template int nufft_inverse_fft<float>(Plan&, float*, cudaStream_t);
-template int nufft_inverse_fft<double>(Plan&, double*, cudaStream_t);
+template int nufft_inverse_fft<float>(Plan&, float*, cudaStream_t, bool);
+template int nufft_inverse_fft<double>(Plan&, double*, cudaStream_t, bool);
+template int split_smooth_part<float>(Plan&, const float*, float*, cudaStream_t);
+template int split_smooth_part<double>(Plan&, const double*, double*, cudaStream_t);
 
 }  // namespace ddi

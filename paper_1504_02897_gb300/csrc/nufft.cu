@@ -544,9 +544,9 @@ int run_type2(Plan& p, const T* rho, cudaStream_t s) {
 }
 
 template <typename T>
-int run_type1(Plan& p, T* phi, cudaStream_t s) {
+int run_type1(Plan& p, T* phi, cudaStream_t s, bool acc = false) {
   DDI_TRY((p.dim == 3 ? launch_spread_w<T, 3>(p, s) : launch_spread_w<T, 2>(p, s)));
-  return nufft_inverse_fft<T>(p, phi, s);
+  return nufft_inverse_fft<T>(p, phi, s, acc);
 }
 
 template <typename T>
@@ -557,7 +557,12 @@ int run_type1_from_c(Plan& p, T* phi, cudaStream_t s) {
 template <typename T>
 int run_ddi(Plan& p, const T* rho, T* phi, cudaStream_t s) {
   DDI_TRY(run_type2<T>(p, rho, s));
-  return run_type1<T>(p, phi, s);
+  if (!p.split()) return run_type1<T>(p, phi, s);
+  // split plans (Eq. 3.9): the ball's node values are in d_c, so the fine grid is free for
+  // the smooth part I_1 until the spread; I_1 reads rho before it writes phi (which may
+  // alias rho), and the ball's part I_2 is added to it
+  DDI_TRY(split_smooth_part<T>(p, rho, phi, s));
+  return run_type1<T>(p, phi, s, /*acc=*/true);
 }
 
 template int run_type2<float>(Plan&, const float*, cudaStream_t);

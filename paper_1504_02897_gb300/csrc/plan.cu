@@ -91,7 +91,8 @@ void choose_tile(Plan& p) {
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_dirw,   p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_fine,  p.d_partial,
+  void* ptrs[] = {p.d_dirw,   p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_ones,  p.d_fine,
+                  p.d_partial,
                   p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
                   p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out};
   for (void* q : ptrs)
@@ -347,6 +348,12 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
     DDI_TRY(upload(p, (void**)&p.d_dirw, dirw, "node directions", stream));
   }
   DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
+  std::vector<float> k4;
+  std::vector<double> ones;
+  if (p.split()) {
+    ones.assign((size_t)p.n[0] + p.n[1] + p.n[2], 1.0);
+    DDI_TRY(upload_real(p, &p.d_ones, ones, "unit factors", stream, &k4));
+  }
   DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
   DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
   DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
@@ -465,6 +472,7 @@ void fill_info(const Plan& p, ddi_plan_info* info) {
   info->nphi = p.desc.nphi;
   info->device_bytes = p.bytes;
   info->spread_tuned_ms = p.tuned_ms;
+  info->split_k0 = p.split() ? p.desc.split_k0 : 0.0;
 }
 
 void destroy_plan(Plan& p) { free_plan(p); }

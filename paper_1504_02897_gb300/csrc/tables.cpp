@@ -1,10 +1,12 @@
 // Quadrature tables of Sec. 2.1 (Eq. DDI-Trun1), built on the host in FP64.
 //
 // Every expression is written in a fixed evaluation order using +, -, *, / and sqrt
-// after the libm cos/sin calls, and this file is compiled with -ffp-contract=off, so
-// the tables are reproducible bit for bit by any implementation of the same rule.
+// after the libm cos/sin calls (and exp, for the window of split plans), and this file is
+// compiled with -ffp-contract=off, so the tables are reproducible bit for bit by any
+// implementation of the same rule on the same libm.
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -108,6 +110,31 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
   }
   int nmax = 0;
   for (int a = 0; a < d.dim; ++a) nmax = d.n[a] > nmax ? d.n[a] : nmax;
+  if (!std::isfinite(d.split_k0)) {
+    *err = "split_k0 must be finite";
+    return DDI_ERR_ARG;
+  }
+  if (d.split_k0 != 0.0) {
+    // the split algorithm of Sec. 2.1 (Eq. 3.9): window width, ball radius and ball rule
+    if (d.dim != 3) {
+      *err = "the split algorithm (split_k0 != 0) is built for 3D plans";
+      return DDI_ERR_ARG;
+    }
+    if (d.split_k0 < 0.0) {
+      const double lmin = std::min(std::min(d.len[0], d.len[1]), d.len[2]);
+      d.split_k0 = 9.6 / lmin;
+    }
+    if (d.kmax == 0.0) d.kmax = 6.0 * d.split_k0;
+    const double diag = std::sqrt((d.len[0] * d.len[0] + d.len[1] * d.len[1]) + d.len[2] * d.len[2]);
+    const double K = d.kmax * diag;
+    auto size_for = [](double v, int least) {
+      const double c = std::ceil(std::min(v, 1e6) / 8.0) * 8.0;
+      return c < (double)least ? least : (int)c;
+    };
+    if (d.nr == 0) d.nr = size_for(0.48 * K, 16);
+    if (d.ntheta == 0) d.ntheta = size_for(0.32 * K, 8);
+    if (d.nphi == 0) d.nphi = size_for(0.64 * K, 16);
+  }
   if (d.dim == 3) {
     if (d.nr == 0) d.nr = nmax;
     if (d.ntheta == 0) d.ntheta = nmax / 2;
@@ -129,7 +156,10 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
   }
   if (d.kmax == 0.0) d.kmax = M_PI / hmin;
   if (!(d.kmax > 0.0) || !std::isfinite(d.kmax) || d.kmax > M_PI / hmin * (1.0 + 1e-12)) {
-    *err = "kmax must be in (0, pi / min h]: the nodes must stay inside the fine grid's band";
+    *err = d.split_k0 != 0.0
+               ? "kmax (default 6 split_k0) must be in (0, pi / min h]: refine the grid or give a smaller "
+                 "split_k0 or kmax"
+               : "kmax must be in (0, pi / min h]: the nodes must stay inside the fine grid's band";
     return DDI_ERR_ARG;
   }
   if (d.precision != DDI_FP64 && d.precision != DDI_FP32) {
@@ -189,6 +219,9 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs) {
     for (int j = 0; j < d.ntheta; ++j) st[j] = std::sqrt((1.0 - u[j]) * (1.0 + u[j]));
     const double nm = (n0 * m0 + n1 * m1) + n2 * m2;
     const double tp3 = (kTwoPi * kTwoPi) * kTwoPi;
+    // split plans (Eq. 3.9): every weight carries the window q(k) = exp(-|k|^2 / k0^2)
+    const bool window = d.split_k0 > 0.0;
+    const double k02 = d.split_k0 * d.split_k0;
     t->M = (int64_t)d.nr * d.ntheta * d.nphi;
     t->k.resize(3 * t->M);
     t->W.resize(t->M);
@@ -206,13 +239,18 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs) {
           const double nk = (n0 * hx + n1 * hy) + n2 * hz;
           const double mk = (m0 * hx + m1 * hy) + m2 * hz;
           const double sym = 3.0 * (nk * mk) - nm;
-          t->W[q] = (wgt * sym) / tp3;
+          double wq = wgt;
+          if (window) {
+            const double kx = t->k[3 * q + 0], ky = t->k[3 * q + 1], kz = t->k[3 * q + 2];
+            wq = wgt * std::exp(-(((kx * kx + ky * ky) + kz * kz) / k02));
+          }
+          t->W[q] = (wq * sym) / tp3;
           if (keep_dirs) {
             double* o = &t->dirw[4 * q];
             o[0] = hx;
             o[1] = hy;
             o[2] = hz;
-            o[3] = wgt;
+            o[3] = wq;
           }
         }
       }

@@ -141,3 +141,94 @@ def test_header_is_plain_c(tmp_path):
                         "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert subprocess.run([str(exe)]).returncode == 0
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    # the ctypes mirrors of the header's structs have the C sizes and field offsets
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1504_02897_gb300 import ddi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = [("ddi_plan_desc", ddi.PlanDesc), ("ddi_plan_info", ddi.PlanInfo), ("gpe_stats", ddi.GpeStats),
+              ("gpe_nonlinearity", ddi.GpeNonlinearity)]
+    lines = ['#include "ddi.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
+    for cname, _ in checks:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+    for cname, py in checks:
+        for f, _ in py._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(py) for _, py in checks]
+    for _, py in checks:
+        want += [getattr(py, f).offset for f, _ in py._fields_]
+    assert got == want
+
+
+# ---- the split algorithm's ball tables (Sec. 2.1, Eq. 3.9) ---------------------------------------
+
+SPLIT_CASES = [
+    dict(n=(32, 32, 32), lo=(-8,) * 3, length=(16,) * 3, axis=(0, 0, 1), m=None, k0=0.8, sizes=(48, 32, 64)),
+    dict(n=(64, 32, 48), lo=(-6, -3, -5), length=(12, 7, 10), axis=(0.5, 0, math.sqrt(0.75)),
+         m=(0.6, 0.0, 0.8), k0=1.3, sizes=(24, 16, 40)),
+]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES)
+def test_split_ball_tables_match_oracle(lib, case):
+    # nodes bit for bit (the spherical rule on |k| <= 6 k0); weights W_q q(k_q) to a few ulp
+    # (the library folds the window into the weight before the symbol, the oracle after it)
+    from oracle import split
+    axis = np.array(case["axis"], float)
+    axis /= np.linalg.norm(axis)
+    m = None if case["m"] is None else np.array(case["m"], float) / np.linalg.norm(case["m"])
+    nr, nt, npp = case["sizes"]
+    desc = lib.make_desc(3, case["n"], case["lo"], case["length"], axis, m, nr=nr, ntheta=nt, nphi=npp,
+                         precision=0, split_k0=case["k0"])
+    k, W, l0 = lib.quadrature_tables(desc)
+    ref = split.ball_tables(case["n"], case["length"], axis, m, k0=case["k0"], nr=nr, ntheta=nt, nphi=npp)
+    assert np.array_equal(k, ref["k"])
+    assert np.max(np.abs(W - ref["W"])) <= 1e-15 * np.max(np.abs(ref["W"]))
+    assert np.all(np.abs(W - ref["W"]) <= 4 * np.spacing(np.abs(ref["W"])))
+    h = [case["length"][d] / case["n"][d] for d in range(3)]
+    assert np.array_equal(l0.astype(np.int64), qd.fine_grid_start(ref["k"], h, [2 * v for v in case["n"]], 14))
+
+
+def test_split_defaults(lib):
+    # k0 = 9.6 / min len, ball 6 k0, sizes 0.48 K / 0.32 K / 0.64 K rounded up to multiples of 8,
+    # K = 6 k0 times the box diagonal: on [-12, 12)^3, k0 = 0.4, K = 2.4 * 24 sqrt(3) = 99.8
+    desc = lib.make_desc(3, (128,) * 3, (-12,) * 3, (24,) * 3, (0.5, 0, math.sqrt(0.75)), precision=1, split_k0=-1)
+    k, W, _ = lib.quadrature_tables(desc)
+    assert k.shape == (48 * 32 * 64, 3)
+    r = np.linalg.norm(k, axis=1)
+    assert r.max() < 2.4 and r.max() > 2.39
+    ref = lib.make_desc(3, (128,) * 3, (-12,) * 3, (24,) * 3, (0.5, 0, math.sqrt(0.75)), precision=1,
+                        split_k0=9.6 / 24, kmax=6 * (9.6 / 24), nr=48, ntheta=32, nphi=64)
+    k2, W2, _ = lib.quadrature_tables(ref)
+    assert np.array_equal(k, k2) and np.array_equal(W, W2)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=2, n=(64, 64), split_k0=1.0),            # 3D only
+    dict(n=(8, 8, 8), split_k0=-1.0),                 # 6 k0 beyond the band of a coarse grid
+    dict(split_k0=float("nan")),
+    dict(split_k0=1.0, kmax=100.0),
+])
+def test_split_descriptor_validation(lib, bad):
+    args = dict(dim=3, n=(32, 32, 32), lo=(-8,) * 3, length=(16,) * 3, split_k0=0.0, kmax=0.0)
+    args.update(bad)
+    dim = args["dim"]
+    desc = lib.make_desc(dim, args["n"], args["lo"][:dim], args["length"][:dim], (0, 0, 1), precision=0,
+                         split_k0=args["split_k0"], kmax=args["kmax"])
+    with pytest.raises(lib.DDIError) as e:
+        lib.quadrature_tables(desc)
+    assert e.value.status == -1

@@ -85,6 +85,13 @@ typedef struct {
                           Quadrature sizes 0 => nr = 0.48 K, ntheta = 0.32 K, nphi = 0.64 K, each
                           rounded up to a multiple of 8 and at least (16, 8, 16), K = kmax times the
                           box diagonal (the phase range of e^{ik.x} the ball rule has to resolve). */
+  int ellipsoid;       /* 0 => the rule on the ball |k| <= kmax.  1 => the same rule mapped onto the
+                          ellipsoid with semi-axes kmax e_d, e_d = min h / h_d (pi / h_d by default), for
+                          heterogeneous boxes such as the thin domains D_eps of Sec. 2.1 (h_z = eps h_x):
+                          nodes e * (r khat), Jacobian e_x e_y (e_z), symbol at the direction of k, and
+                          in 2D the symbol's factor |k| = r |e * khat|.  Default polar (3D) / azimuthal
+                          (2D) size ceil(N/2 ratio) / 2 ceil(N ratio), ratio = max h / min h.  Not
+                          combined with split_k0. */
 } ddi_plan_desc;
 
 /* Read-only facts about a built plan (sizes and the NUFFT parameters chosen). */

@@ -16,6 +16,15 @@ quadratures"; the rule used here (the same rule the CUDA library builds) is:
   so the node set is closed under k -> -k bit for bit;
 * R = k_max = pi / min_d h_d unless given.
 
+Heterogeneous boxes (h_d unequal, e.g. the thin domains D_eps of Sec. 2.1 with
+h_z = eps h_x): ``ellipsoid=True`` maps the same rule onto the ellipsoid with semi-axes
+a_d = R e_d, e_d = min h / h_d (a_d = pi / h_d by default), i.e. k = e * (r khat_ball).
+The Jacobian is e_x e_y (e_z); the symbol is evaluated at the direction of k,
+g / |g| with g = e * khat_ball; in 2D the symbol's factor |k| is r |g|.  With equal h_d
+the rule is the spherical one up to the rounding of |g| = 1.  Default polar (3D) or
+azimuthal (2D) size grows with max h / min h, because the symbol at the direction of k
+turns over an angular band of width ~ min e / max e of the unit sphere.
+
 Weights of the discrete sum (so that Phi_j = Re sum_q W_q e^{i k_q.x_j} rhohat_q):
     3D: W_q = w_r w_u w_phi |k|^2 [3 (n.khat)(m.khat) - n.m] / (2 pi)^3
     2D: W_q = w_r w_phi |k| * 3[(n_perp.k)(m_perp.k) - n3 m3 |k|^2] / (2|k|) / (2 pi)^2
@@ -83,11 +92,17 @@ def gauss_legendre(n):
     return x, wt
 
 
-def default_sizes(dim, n):
-    """Default quadrature sizes: (N, N/2, N) in 3D and (2N, -, 2N) in 2D (N = max grid size)."""
+def default_sizes(dim, n, ratio=None):
+    """Default quadrature sizes: (N, N/2, N) in 3D and (2N, -, 2N) in 2D (N = max grid size).
+    ratio = max h / min h of an ellipsoidal rule: the 3D polar size becomes ceil(N/2 ratio),
+    the 2D azimuthal size 2 ceil(N ratio)."""
     nmax = max(n[:dim])
     if dim == 3:
+        if ratio is not None:
+            return nmax, int(math.ceil(0.5 * nmax * ratio)), nmax
         return nmax, nmax // 2, nmax
+    if ratio is not None:
+        return 2 * nmax, 1, 2 * int(math.ceil(nmax * ratio))
     return 2 * nmax, 1, 2 * nmax
 
 
@@ -107,19 +122,23 @@ def azimuth_table(nphi):
     return c, s
 
 
-def plan_tables(dim, n, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0):
+def plan_tables(dim, n, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0, ellipsoid=False):
     """Quadrature nodes k_q (M x dim) and DDI weights W_q (M,) in node order.
 
     Node order: q = (i_r * n_theta + j_u) * n_phi + m in 3D, q = i_r * n_phi + m in 2D.
     ``n``/``length``: grid sizes and box lengths per axis; h_d = length_d / n_d.
+    ``ellipsoid``: the rule mapped onto the ellipsoid with semi-axes R min h / h_d.
     """
     if axis_m is None:
         axis_m = axis_n
-    dnr, dnt, dnp = default_sizes(dim, n)
+    h = [length[d] / n[d] for d in range(dim)]
+    hmin = min(h)
+    dnr, dnt, dnp = default_sizes(dim, n, max(h) / hmin if ellipsoid else None)
     nr = nr or dnr
     ntheta = ntheta or dnt
     nphi = nphi or dnp
-    h = [length[d] / n[d] for d in range(dim)]
+    if ellipsoid:
+        return _ellipsoid_tables(dim, h, hmin, axis_n, axis_m, nr, ntheta, nphi, kmax)
     if not kmax:
         kmax = math.pi / min(h)
     R = float(kmax)
@@ -170,6 +189,71 @@ def plan_tables(dim, n, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kma
     k = np.stack([kx.ravel(), ky.ravel()], axis=1)
     return {"k": k, "W": np.ascontiguousarray(W).ravel(), "R": R,
             "sizes": (nr, 1, nphi), "h": h}
+
+
+def _ellipsoid_tables(dim, h, hmin, axis_n, axis_m, nr, ntheta, nphi, kmax):
+    """The rule of ``plan_tables`` on the ellipsoid |k_d| <= R e_d, e_d = min h / h_d: nodes
+    e * (r khat), weight w_r (w_u) w_phi r^2 (e_x e_y e_z) Uhat(g / |g|) / (2 pi)^3 in 3D and
+    w_r w_phi r^2 (e_x e_y) |g| * 1.5 [(n_perp.ghat)(m_perp.ghat) - n3 m3] / (2 pi)^2 in 2D,
+    g = e * khat; written as loops in the order the library evaluates them."""
+    R = float(kmax) if kmax else math.pi / hmin
+    e = [hmin / h[d] for d in range(dim)]
+    xr, wr0 = gauss_legendre(nr)
+    half_R = 0.5 * R
+    r = [half_R * (1.0 + x) for x in xr]
+    wr = [half_R * w for w in wr0]
+    c, s = azimuth_table(nphi)
+    wphi = TWO_PI / nphi
+    n0, n1, n2 = (float(v) for v in axis_n)
+    m0, m1, m2 = (float(v) for v in axis_m)
+    if dim == 3:
+        u, wu = gauss_legendre(ntheta)
+        st = [math.sqrt((1.0 - v) * (1.0 + v)) for v in u]
+        J = (e[0] * e[1]) * e[2]
+        nm = (n0 * m0 + n1 * m1) + n2 * m2
+        tp3 = (TWO_PI * TWO_PI) * TWO_PI
+        M = nr * ntheta * nphi
+        k = np.empty((M, 3))
+        W = np.empty(M)
+        q = 0
+        for i in range(nr):
+            for j in range(ntheta):
+                rst = r[i] * st[j]
+                wgt = (((wr[i] * wu[j]) * wphi) * (r[i] * r[i])) * J
+                for mm in range(nphi):
+                    k[q, 0] = (rst * c[mm]) * e[0]
+                    k[q, 1] = (rst * s[mm]) * e[1]
+                    k[q, 2] = (r[i] * u[j]) * e[2]
+                    gx = (st[j] * c[mm]) * e[0]
+                    gy = (st[j] * s[mm]) * e[1]
+                    gz = u[j] * e[2]
+                    gn = math.sqrt((gx * gx + gy * gy) + gz * gz)
+                    hx, hy, hz = gx / gn, gy / gn, gz / gn
+                    nk = (n0 * hx + n1 * hy) + n2 * hz
+                    mk = (m0 * hx + m1 * hy) + m2 * hz
+                    W[q] = (wgt * (3.0 * (nk * mk) - nm)) / tp3
+                    q += 1
+        return {"k": k, "W": W, "R": R, "sizes": (nr, ntheta, nphi), "h": h, "e": e}
+    J = e[0] * e[1]
+    tp2 = TWO_PI * TWO_PI
+    M = nr * nphi
+    k = np.empty((M, 2))
+    W = np.empty(M)
+    q = 0
+    for i in range(nr):
+        w0 = ((wr[i] * wphi) * (r[i] * r[i])) * J
+        for mm in range(nphi):
+            k[q, 0] = (r[i] * c[mm]) * e[0]
+            k[q, 1] = (r[i] * s[mm]) * e[1]
+            gx = c[mm] * e[0]
+            gy = s[mm] * e[1]
+            gn = math.sqrt(gx * gx + gy * gy)
+            hx, hy = gx / gn, gy / gn
+            nk = n0 * hx + n1 * hy
+            mk = m0 * hx + m1 * hy
+            W[q] = ((w0 * gn) * (1.5 * (nk * mk - n2 * m2))) / tp2
+            q += 1
+    return {"k": k, "W": W, "R": R, "sizes": (nr, 1, nphi), "h": h, "e": e}
 
 
 def fine_grid_start(k, h, nf, width):

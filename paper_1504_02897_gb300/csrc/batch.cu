@@ -41,9 +41,9 @@ std::string tune_key_of(const Plan& p) {
   double kh[3] = {0.0, 0.0, 0.0};
   for (int a = 0; a < p.dim; ++a) kh[a] = p.desc.kmax * p.h[a];
   char buf[320];
-  snprintf(buf, sizeof buf, "dev%d dim%d prec%d w%d n%d,%d,%d q%d,%d,%d kh%.12g,%.12g,%.12g chunk%d", p.device,
+  snprintf(buf, sizeof buf, "dev%d dim%d prec%d w%d n%d,%d,%d q%d,%d,%d kh%.12g,%.12g,%.12g chunk%d ell%d", p.device,
            p.dim, p.prec, p.w, p.n[0], p.n[1], p.n[2], p.desc.nr, p.desc.ntheta, p.desc.nphi, kh[0], kh[1], kh[2],
-           p.desc.chunk);
+           p.desc.chunk, p.desc.ellipsoid);
   return buf;
 }
 

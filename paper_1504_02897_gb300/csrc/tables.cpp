@@ -135,6 +135,27 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
     if (d.ntheta == 0) d.ntheta = size_for(0.32 * K, 8);
     if (d.nphi == 0) d.nphi = size_for(0.64 * K, 16);
   }
+  if (d.ellipsoid != 0 && d.ellipsoid != 1) {
+    *err = "ellipsoid must be 0 or 1";
+    return DDI_ERR_ARG;
+  }
+  if (d.ellipsoid && d.split_k0 != 0.0) {
+    *err = "the ellipsoidal rule is not combined with the split algorithm";
+    return DDI_ERR_ARG;
+  }
+  if (d.ellipsoid) {
+    // the symbol at the direction of k turns over an angular band ~ min e / max e wide
+    double hlo = 1e300, hhi = 0.0;
+    for (int a = 0; a < d.dim; ++a) {
+      const double h = d.len[a] / (double)d.n[a];
+      hlo = h < hlo ? h : hlo;
+      hhi = h > hhi ? h : hhi;
+    }
+    const double ratio = hhi / hlo;
+    const double big = 1e6;
+    if (d.dim == 3 && d.ntheta == 0) d.ntheta = (int)std::ceil(std::min(0.5 * nmax * ratio, big));
+    if (d.dim == 2 && d.nphi == 0) d.nphi = 2 * (int)std::ceil(std::min(nmax * ratio, big));
+  }
   if (d.dim == 3) {
     if (d.nr == 0) d.nr = nmax;
     if (d.ntheta == 0) d.ntheta = nmax / 2;
@@ -222,6 +243,15 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs) {
     // split plans (Eq. 3.9): every weight carries the window q(k) = exp(-|k|^2 / k0^2)
     const bool window = d.split_k0 > 0.0;
     const double k02 = d.split_k0 * d.split_k0;
+    // ellipsoidal rule: nodes e * (r khat), Jacobian e_x e_y e_z, symbol at g / |g|, g = e * khat
+    const bool ell = d.ellipsoid != 0;
+    double e[3] = {1.0, 1.0, 1.0};
+    if (ell) {
+      double hmin = t->h[0];
+      for (int a = 1; a < 3; ++a) hmin = t->h[a] < hmin ? t->h[a] : hmin;
+      for (int a = 0; a < 3; ++a) e[a] = hmin / t->h[a];
+    }
+    const double J = (e[0] * e[1]) * e[2];
     t->M = (int64_t)d.nr * d.ntheta * d.nphi;
     t->k.resize(3 * t->M);
     t->W.resize(t->M);
@@ -230,12 +260,27 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs) {
     for (int i = 0; i < d.nr; ++i) {
       for (int j = 0; j < d.ntheta; ++j) {
         const double rst = r[i] * st[j];
-        const double wgt = ((wr[i] * wu[j]) * wphi) * (r[i] * r[i]);
+        double wgt = ((wr[i] * wu[j]) * wphi) * (r[i] * r[i]);
+        if (ell) wgt = wgt * J;
         for (int m = 0; m < d.nphi; ++m, ++q) {
-          t->k[3 * q + 0] = rst * c[m];
-          t->k[3 * q + 1] = rst * s[m];
-          t->k[3 * q + 2] = r[i] * u[j];
-          const double hx = st[j] * c[m], hy = st[j] * s[m], hz = u[j];
+          double hx, hy, hz;
+          if (!ell) {
+            t->k[3 * q + 0] = rst * c[m];
+            t->k[3 * q + 1] = rst * s[m];
+            t->k[3 * q + 2] = r[i] * u[j];
+            hx = st[j] * c[m];
+            hy = st[j] * s[m];
+            hz = u[j];
+          } else {
+            t->k[3 * q + 0] = (rst * c[m]) * e[0];
+            t->k[3 * q + 1] = (rst * s[m]) * e[1];
+            t->k[3 * q + 2] = (r[i] * u[j]) * e[2];
+            const double gx = (st[j] * c[m]) * e[0], gy = (st[j] * s[m]) * e[1], gz = u[j] * e[2];
+            const double gn = std::sqrt((gx * gx + gy * gy) + gz * gz);
+            hx = gx / gn;
+            hy = gy / gn;
+            hz = gz / gn;
+          }
           const double nk = (n0 * hx + n1 * hy) + n2 * hz;
           const double mk = (m0 * hx + m1 * hy) + m2 * hz;
           const double sym = 3.0 * (nk * mk) - nm;
@@ -262,21 +307,43 @@ void build_quadrature(const ddi_plan_desc& d, QuadTables* t, bool keep_dirs) {
     t->W.resize(t->M);
     if (keep_dirs) t->dirw.resize(4 * t->M);
     int64_t q = 0;
+    // ellipsoidal rule: nodes e * (r khat), Jacobian e_x e_y, symbol factor |k| = r |g|,
+    // symbol direction g / |g|, g = e * khat
+    const bool ell = d.ellipsoid != 0;
+    double e[2] = {1.0, 1.0};
+    if (ell) {
+      const double hmin = t->h[0] < t->h[1] ? t->h[0] : t->h[1];
+      e[0] = hmin / t->h[0];
+      e[1] = hmin / t->h[1];
+    }
+    const double J = e[0] * e[1];
     for (int i = 0; i < d.nr; ++i) {
-      const double wgt = (wr[i] * wphi) * (r[i] * r[i]);
+      double wgt = (wr[i] * wphi) * (r[i] * r[i]);
+      if (ell) wgt = wgt * J;
       for (int m = 0; m < d.nphi; ++m, ++q) {
-        t->k[2 * q + 0] = r[i] * c[m];
-        t->k[2 * q + 1] = r[i] * s[m];
-        const double nk = n0 * c[m] + n1 * s[m];
-        const double mk = m0 * c[m] + m1 * s[m];
+        double hx = c[m], hy = s[m], wq = wgt;
+        if (!ell) {
+          t->k[2 * q + 0] = r[i] * c[m];
+          t->k[2 * q + 1] = r[i] * s[m];
+        } else {
+          t->k[2 * q + 0] = (r[i] * c[m]) * e[0];
+          t->k[2 * q + 1] = (r[i] * s[m]) * e[1];
+          const double gx = c[m] * e[0], gy = s[m] * e[1];
+          const double gn = std::sqrt(gx * gx + gy * gy);
+          hx = gx / gn;
+          hy = gy / gn;
+          wq = wgt * gn;
+        }
+        const double nk = n0 * hx + n1 * hy;
+        const double mk = m0 * hx + m1 * hy;
         const double sym = 1.5 * (nk * mk - n2 * m2);
-        t->W[q] = (wgt * sym) / tp2;
+        t->W[q] = (wq * sym) / tp2;
         if (keep_dirs) {
           double* o = &t->dirw[4 * q];
-          o[0] = c[m];
-          o[1] = s[m];
+          o[0] = hx;
+          o[1] = hy;
           o[2] = 0.0;
-          o[3] = wgt;
+          o[3] = wq;
         }
       }
     }

@@ -35,7 +35,8 @@ class PlanDesc(ctypes.Structure):
                 ("len", ctypes.c_double * 3), ("axis_n", ctypes.c_double * 3), ("axis_m", ctypes.c_double * 3),
                 ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
                 ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
-                ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("split_k0", ctypes.c_double)]
+                ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("split_k0", ctypes.c_double),
+                ("ellipsoid", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -135,11 +136,12 @@ def _check(status, where):
 
 
 def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
-              precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0):
+              precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0, ellipsoid=False):
     """A plan descriptor (``ddi_plan_desc``).  split_k0 != 0 selects the improved split
     algorithm of Sec. 2.1 (Eq. 3.9), 3D only: window q = exp(-|k|^2/k0^2) with k0 = split_k0
     (< 0: the library's default), the quadrature on the small ball |k| <= kmax (0: 6 k0)
-    and the smooth part by a zero-padded FFT convolution."""
+    and the smooth part by a zero-padded FFT convolution.  ellipsoid: the quadrature on the
+    ellipsoid |k_d| <= pi / h_d (heterogeneous boxes, e.g. thin domains h_z = eps h_x)."""
     d = PlanDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -158,6 +160,7 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.nufft_tol = float(nufft_tol)
     d.chunk = int(chunk)
     d.split_k0 = float(split_k0)
+    d.ellipsoid = 1 if ellipsoid else 0
     return d
 
 

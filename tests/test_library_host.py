@@ -232,3 +232,55 @@ def test_split_descriptor_validation(lib, bad):
     with pytest.raises(lib.DDIError) as e:
         lib.quadrature_tables(desc)
     assert e.value.status == -1
+
+
+# ---- the ellipsoidal rule for heterogeneous boxes ------------------------------------------------
+
+ELL_CASES = [
+    # thin 3D box D_eps = [-8,8]^2 x [-2,2] (eps = 1/4, h_z = h_x / 4), default sizes (32, 64, 32)
+    dict(dim=3, n=(32, 32, 32), lo=(-8, -8, -2), length=(16, 16, 4), axis=(0, 0, 1), m=None, sizes=(0, 0, 0)),
+    # ragged 3D box, two axes, explicit sizes
+    dict(dim=3, n=(32, 16, 64), lo=(-4, -2, -8), length=(8, 3, 16), axis=(0.5, 0, math.sqrt(0.75)),
+         m=(0.6, 0.0, 0.8), sizes=(24, 20, 36)),
+    # thin 2D rectangle [-8,8] x [-2,2] with the axes of Example 2d_exmp, default sizes (128, -, 512)
+    dict(dim=2, n=(64, 64), lo=(-8, -2), length=(16, 4), axis=(0, -0.896, 0.44404), m=(0, -0.52476, 0.85125),
+         sizes=(0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("case", ELL_CASES)
+def test_ellipsoid_tables_bitwise_equal_oracle(lib, case):
+    axis = np.array(case["axis"], float)
+    axis /= np.linalg.norm(axis)
+    m = None if case["m"] is None else np.array(case["m"], float) / np.linalg.norm(case["m"])
+    nr, nt, npp = case["sizes"]
+    desc = lib.make_desc(case["dim"], case["n"], case["lo"], case["length"], axis, m, nr=nr, ntheta=nt, nphi=npp,
+                         precision=0, ellipsoid=True)
+    k, W, l0 = lib.quadrature_tables(desc)
+    ref = qd.plan_tables(case["dim"], case["n"], case["length"], axis, m, nr=nr, ntheta=nt, nphi=npp, ellipsoid=True)
+    assert k.shape == ref["k"].shape
+    assert np.array_equal(k, ref["k"]), np.max(np.abs(k - ref["k"]))
+    assert np.array_equal(W, ref["W"]), np.max(np.abs(W - ref["W"]))
+    nf = [2 * v for v in case["n"]]
+    assert np.array_equal(l0.astype(np.int64), qd.fine_grid_start(ref["k"], ref["h"], nf, 14))
+    # every node stays inside its own axis' band |k_d| <= pi / h_d
+    for d in range(case["dim"]):
+        assert np.max(np.abs(k[:, d])) * ref["h"][d] <= math.pi * (1 + 1e-15)
+
+
+def test_ellipsoid_defaults(lib):
+    desc = lib.make_desc(3, (32, 32, 32), (-8, -8, -2), (16, 16, 4), (0, 0, 1), ellipsoid=True)
+    k, _, _ = lib.quadrature_tables(desc)
+    assert k.shape[0] == 32 * 64 * 32          # ceil(32/2 * 4) polar nodes
+    desc = lib.make_desc(2, (64, 64), (-8, -2), (16, 4), (1, 0, 0), ellipsoid=True)
+    k, _, _ = lib.quadrature_tables(desc)
+    assert k.shape[0] == 128 * 512             # 2 ceil(64 * 4) azimuthal nodes
+
+
+@pytest.mark.parametrize("bad", [dict(ellipsoid=2), dict(ellipsoid=1, split_k0=1.0)])
+def test_ellipsoid_descriptor_validation(lib, bad):
+    desc = lib.make_desc(3, (32, 32, 32), (-8,) * 3, (16,) * 3, (0, 0, 1), split_k0=bad.get("split_k0", 0.0))
+    desc.ellipsoid = bad["ellipsoid"]
+    with pytest.raises(lib.DDIError) as e:
+        lib.quadrature_tables(desc)
+    assert e.value.status == -1

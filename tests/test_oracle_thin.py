@@ -54,6 +54,27 @@ def test_thin_3d_box_matches_closed_form():
     assert np.max(np.abs(got[sel] - ex)) / np.max(np.abs(ex)) <= 1e-7
 
 
+def test_thin_3d_box_localised_in_two_directions():
+    # the second kind of Eq. Coulomb:3D:aniso:xy: rho = exp(-(x^2+y^2)/(4 eps^2) - z^2/4) /
+    # (8 pi^1.5 eps^2) on [-2,2]^2 x [-8,8] (eps = 1/4), h_x = h_y = eps h_z, h_z = 1/2: the
+    # oblate ellipsoid resolves it to the same truncation level
+    eps, L = 0.25, 8.0
+    n = (32, 32, 32)
+    lo = (-eps * L, -eps * L, -L)
+    ln = (2 * eps * L, 2 * eps * L, 2 * L)
+    ax = [lo[d] + np.arange(n[d]) * (ln[d] / n[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    s2 = [2.0 * eps * eps, 2.0 * eps * eps, 2.0]
+    rho = cf.gaussian_density(pts, s2, [0, 0, 0], 1.0).reshape(X.shape)
+    nax = np.array([0.0, 0.0, 1.0])
+    t = qd.plan_tables(3, n, ln, nax, nr=96, ntheta=48, nphi=96, ellipsoid=True)
+    got = nudft.ddi(rho, t, n, lo, ln).ravel()
+    sel = np.random.default_rng(0).choice(pts.shape[0], 300, replace=False)
+    ex = cf.phi3d_gauss_integral(pts[sel], s2, [0, 0, 0], nax, None, mass=1.0)
+    assert np.max(np.abs(got[sel] - ex)) / np.max(np.abs(ex)) <= 1e-7
+
+
 def test_thin_2d_box_matches_closed_form_to_the_papers_accuracy():
     # rho = exp(-x^2/4 - y^2/(4 eps^2)) / (4 pi eps) (Eq. Coulomb:2D:aniso), axes of Example
     # 2d_exmp, D_eps = [-16,16] x [-4,4] (eps = 1/4), h_x = 1/4, h_y = eps h_x.  Table ani_2d

@@ -76,6 +76,30 @@ def test_split_matches_erf_closed_form():
     assert np.max(np.abs(got - ex)) / np.max(np.abs(ex)) <= bound
 
 
+def test_split_two_axes_matches_erf_closed_form():
+    # the axes n != m of Table tab:diff:dip (Eq. dipmn) with the Erf form of the same Gaussian:
+    # p carries 3 (n.k)(m.k) - (n.m)|k|^2 and the ball weights the two-axis symbol, so an axis
+    # used twice or a dropped n.m term in either part fails this
+    import json
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+    tab = json.load(open(golden))["tab:diff:dip"]["setup"]
+    nax = np.array(tab["n"], float) / np.linalg.norm(tab["n"])
+    m_axis = np.array(tab["m"], float) / np.linalg.norm(tab["m"])
+    n, lo, ln, X, Y, Z = _grid(32, 8.0)
+    sigma = 1.4
+    rho = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / sigma ** 2)
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    ex = cf.phi3d_erf(pts, sigma, nax, m_axis)
+    small = np.linalg.norm(pts, axis=1) < 0.1
+    ex[small] = cf.phi3d_gauss_integral(pts[small], [sigma ** 2 / 2] * 3, [0, 0, 0], nax, m_axis,
+                                        mass=(math.pi * sigma ** 2) ** 1.5)
+    ex = ex.reshape(X.shape)
+    got = split.ddi_split(rho, n, lo, ln, nax, m_axis, k0=0.8, **BALL)
+    bound = math.exp(-sigma ** 2 * (math.pi / 0.5) ** 2 / 4)
+    assert np.max(np.abs(got - ex)) / np.max(np.abs(ex)) <= bound
+
+
 def test_window_width_does_not_matter():
     # the split is exact in the continuum: moving the window (and the ball with it) changes
     # only quadrature errors, which these rules keep at roundoff

@@ -70,7 +70,13 @@ def test_split_matches_oracle(D, name, precision):
     assert plan.info.split_k0 == c["k0"]
     got = plan.apply(_t(c["rho"], plan.real_dtype)).double().cpu().numpy()
     ref = split.ddi_split(c["rho"], c["n"], c["lo"], c["ln"], c["axis"], c["m"], k0=c["k0"], **c["sizes"])
-    assert _relinf(got, ref) <= TOL[precision]
+    tol = TOL[precision]
+    if precision:
+        # the FP32 path cannot beat the rounding of its input: 8x that floor where it exceeds 1e-6
+        r32 = split.ddi_split(c["rho"].astype(np.float32).astype(np.float64), c["n"], c["lo"], c["ln"], c["axis"],
+                              c["m"], k0=c["k0"], **c["sizes"])
+        tol = max(tol, 8.0 * _relinf(r32, ref))
+    assert _relinf(got, ref) <= tol
 
 
 def test_split_parts_through_the_stages(D):

@@ -41,10 +41,11 @@ typedef enum {
   DDI_OK = 0,
   DDI_ERR_ARG = -1,        /* invalid argument (sizes, axes, pointers, precision) */
   DDI_ERR_CUDA = -2,       /* a CUDA runtime call or kernel launch failed */
-  DDI_ERR_OOM = -3,        /* device allocation failed in ddi_plan_create */
+  DDI_ERR_OOM = -3,        /* a device or host allocation failed (plan or batch creation) */
   DDI_ERR_NONFINITE = -4,  /* NaN/Inf found in an input or produced by an iteration */
   DDI_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
-  DDI_ERR_NOCONV = -6      /* an iteration hit its step limit before the tolerance */
+  DDI_ERR_NOCONV = -6,     /* an iteration hit its step limit before the tolerance */
+  DDI_ERR_INTERNAL = -7    /* an unexpected host-side failure inside the library */
 } ddi_status;
 
 enum { DDI_FP64 = 0, DDI_FP32 = 1 };

@@ -210,36 +210,58 @@ int record_graph(ddi_batch_s* b, const void* const* rho, void* const* phi) {
   return DDI_OK;
 }
 
+int build_batch(ddi_batch_s* b, ddi_batch* out, const ddi_plan_desc* descs, int count, int flags, void* stream);
 }  // namespace
 
 extern "C" {
 
 int ddi_batch_create(ddi_batch* out, const ddi_plan_desc* descs, int count, int flags, void* stream) {
-  if (!out || !descs || count <= 0 || (flags & ~(DDI_BATCH_GRAPH | DDI_BATCH_AUTOTUNE)) != 0) {
-    ddi::set_error("ddi_batch_create: out and descs must not be NULL, count > 0, flags a set of DDI_BATCH_*");
-    return DDI_ERR_ARG;
-  }
-  *out = nullptr;
-  ddi_batch_s* b = new (std::nothrow) ddi_batch_s();
-  if (!b) {
-    ddi::set_error("host allocation failed");
-    return DDI_ERR_OOM;
-  }
-  b->flags = flags;
-  if (cudaGetDevice(&b->device) != cudaSuccess) {
-    cudaGetLastError();
-    delete b;
-    ddi::set_error("ddi_batch_create: no current device");
-    return DDI_ERR_CUDA;
-  }
+  return ddi::guarded("ddi_batch_create", [&]() -> int {
+    if (!out || !descs || count <= 0 || (flags & ~(DDI_BATCH_GRAPH | DDI_BATCH_AUTOTUNE)) != 0) {
+      ddi::set_error("ddi_batch_create: out and descs must not be NULL, count > 0, flags a set of DDI_BATCH_*");
+      return DDI_ERR_ARG;
+    }
+    *out = nullptr;
+    ddi_batch_s* b = new (std::nothrow) ddi_batch_s();
+    if (!b) {
+      ddi::set_error("host allocation failed");
+      return DDI_ERR_OOM;
+    }
+    b->flags = flags;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      ddi::set_error("ddi_batch_create: no current device");
+      return DDI_ERR_CUDA;
+    }
+    try {
+      return build_batch(b, out, descs, count, flags, stream);
+    } catch (...) {
+      free_batch(b);  // the plans and streams built before the failure
+      throw;
+    }
+  });
+}
+
+}  // extern "C"
+
+namespace {
+
+// the body of ddi_batch_create once the batch object exists; failures free it (fail())
+int build_batch(ddi_batch_s* b, ddi_batch* out, const ddi_plan_desc* descs, int count, int flags, void* stream) {
   b->plans.assign(count, nullptr);
 
   // plans are built by host threads (their tables and work lists are host work), each
   // with its own upload stream
   std::atomic<int> next{0};
-  std::mutex err_mu;
-  int first_status = DDI_OK;
-  std::string first_msg;
+  // the first failure of any thread, recorded without locks or allocation (nothing in the
+  // threads may throw)
+  std::atomic<int> first_status{DDI_OK};
+  char first_msg[1024] = "";
+  auto record = [&](int st, const char* msg) {
+    int expect = DDI_OK;
+    if (first_status.compare_exchange_strong(expect, st)) snprintf(first_msg, sizeof first_msg, "%s", msg);
+  };
   auto worker = [&]() {
     cudaSetDevice(b->device);
     cudaStream_t s = nullptr;
@@ -253,23 +275,26 @@ int ddi_batch_create(ddi_batch* out, const ddi_plan_desc* descs, int count, int 
         break;
       }
       b->plans[i] = p;
-      st = ddi::create_plan(*p, &descs[i], s, /*gpe=*/false);
+      // an exception must not leave a worker thread
+      st = ddi::guarded("ddi_batch_create", [&]() -> int { return ddi::create_plan(*p, &descs[i], s, false); });
       if (st != DDI_OK) ddi::set_error("batch item %d: %s", i, ddi::last_error());
     }
     if (st != DDI_OK) {
-      std::lock_guard<std::mutex> lock(err_mu);
-      if (first_status == DDI_OK) {
-        first_status = st;
-        first_msg = ddi::last_error();
-      }
+      record(st, ddi::last_error());
       next.store(count);
     }
     if (s) cudaStreamDestroy(s);
   };
   const int nthreads = std::max(1, std::min<int>(count, std::min(16u, std::max(1u, std::thread::hardware_concurrency()))));
   {
+    // the shared counter balances any number of threads: if one cannot be started the
+    // ones running (and this one) take its share
     std::vector<std::thread> pool;
-    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    try {
+      pool.reserve(nthreads);
+      for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    } catch (...) {
+    }
     worker();
     for (auto& t : pool) t.join();
   }
@@ -277,9 +302,9 @@ int ddi_batch_create(ddi_batch* out, const ddi_plan_desc* descs, int count, int 
     free_batch(b);
     return st;
   };
-  if (first_status != DDI_OK) {
-    ddi::set_error("%s", first_msg.c_str());
-    return fail(first_status);
+  if (first_status.load() != DDI_OK) {
+    ddi::set_error("%s", first_msg);
+    return fail(first_status.load());
   }
 
   cudaStream_t s0 = static_cast<cudaStream_t>(stream);
@@ -300,35 +325,31 @@ int ddi_batch_create(ddi_batch* out, const ddi_plan_desc* descs, int count, int 
       cudaSetDevice(b->device);
       cudaStream_t s = nullptr;
       if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-        std::lock_guard<std::mutex> lock(err_mu);
-        if (first_status == DDI_OK) {
-          first_status = DDI_ERR_CUDA;
-          first_msg = "cudaStreamCreate failed";
-        }
+        record(DDI_ERR_CUDA, "cudaStreamCreate failed");
         return;
       }
       for (int j; (j = nt.fetch_add(1)) < (int)tune_items.size();) {
         Plan& p = *b->plans[tune_items[j]];
         if (p.tuned_ms > 0.0) continue;
-        const int st = ddi::tune_spread_tile(p, s);
+        const int st = ddi::guarded("ddi_batch_create", [&]() -> int { return ddi::tune_spread_tile(p, s); });
         if (st != DDI_OK) {
-          std::lock_guard<std::mutex> lock(err_mu);
-          if (first_status == DDI_OK) {
-            first_status = st;
-            first_msg = ddi::last_error();
-          }
+          record(st, ddi::last_error());
           nt.store((int)tune_items.size());
         }
       }
       cudaStreamDestroy(s);
     };
     std::vector<std::thread> pool;
-    for (int t = 1; t < nthreads; ++t) pool.emplace_back(retune);
+    try {
+      pool.reserve(nthreads);
+      for (int t = 1; t < nthreads; ++t) pool.emplace_back(retune);
+    } catch (...) {
+    }
     retune();
     for (auto& t : pool) t.join();
-    if (first_status != DDI_OK) {
-      ddi::set_error("%s", first_msg.c_str());
-      return fail(first_status);
+    if (first_status.load() != DDI_OK) {
+      ddi::set_error("%s", first_msg);
+      return fail(first_status.load());
     }
   }
   // host copies only needed while building
@@ -374,6 +395,10 @@ int ddi_batch_create(ddi_batch* out, const ddi_plan_desc* descs, int count, int 
   return DDI_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 int ddi_batch_destroy(ddi_batch b) {
   if (b) {
     cudaDeviceSynchronize();
@@ -394,23 +419,25 @@ int ddi_batch_get_info(ddi_batch b, int item, ddi_plan_info* info) {
 }
 
 int ddi_batch_apply(ddi_batch b, const void* const* rho, void* const* phi, void* stream) {
-  if (!b || !rho || !phi) {
-    ddi::set_error("ddi_batch_apply: batch, rho and phi must not be NULL");
-    return DDI_ERR_ARG;
-  }
-  const size_t n = b->plans.size();
-  for (size_t i = 0; i < n; ++i)
-    if (!rho[i] || !phi[i]) {
-      ddi::set_error("ddi_batch_apply: rho[%zu] and phi[%zu] must be device pointers", i, i);
+  return ddi::guarded("ddi_batch_apply", [&]() -> int {
+    if (!b || !rho || !phi) {
+      ddi::set_error("ddi_batch_apply: batch, rho and phi must not be NULL");
       return DDI_ERR_ARG;
     }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!(b->flags & DDI_BATCH_GRAPH)) return enqueue(b, rho, phi, s);
-  const bool same = b->exec && std::equal(rho, rho + n, b->g_rho.begin()) && std::equal(phi, phi + n, b->g_phi.begin());
-  if (!same) DDI_TRY(record_graph(b, rho, phi));
-  DDI_CUDA(cudaGraphLaunch(b->exec, s));
-  ++b->replays;
-  return DDI_OK;
+    const size_t n = b->plans.size();
+    for (size_t i = 0; i < n; ++i)
+      if (!rho[i] || !phi[i]) {
+        ddi::set_error("ddi_batch_apply: rho[%zu] and phi[%zu] must be device pointers", i, i);
+        return DDI_ERR_ARG;
+      }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!(b->flags & DDI_BATCH_GRAPH)) return enqueue(b, rho, phi, s);
+    const bool same = b->exec && std::equal(rho, rho + n, b->g_rho.begin()) && std::equal(phi, phi + n, b->g_phi.begin());
+    if (!same) DDI_TRY(record_graph(b, rho, phi));
+    DDI_CUDA(cudaGraphLaunch(b->exec, s));
+    ++b->replays;
+    return DDI_OK;
+  });
 }
 
 int ddi_batch_graph_stats(ddi_batch b, long long* records, long long* launches) {

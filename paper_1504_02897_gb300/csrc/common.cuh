@@ -5,6 +5,8 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -36,6 +38,25 @@ const char* last_error();
       return DDI_ERR_CUDA;                                                              \
     }                                                                                   \
   } while (0)
+
+// Runs f() (returning a status) so that no C++ exception crosses the C ABI: a failed host
+// allocation becomes DDI_ERR_OOM, any other exception DDI_ERR_INTERNAL, with the message
+// kept for ddi_last_error().
+template <typename F>
+int guarded(const char* where, F&& f) noexcept {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    set_error("%s: host allocation failed", where);
+    return DDI_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_error("%s: %s", where, e.what());
+    return DDI_ERR_INTERNAL;
+  } catch (...) {
+    set_error("%s: unknown exception", where);
+    return DDI_ERR_INTERNAL;
+  }
+}
 
 #define DDI_TRY(expr)          \
   do {                         \

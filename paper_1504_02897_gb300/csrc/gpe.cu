@@ -714,100 +714,110 @@ extern "C" {
 
 int gpe_step(ddi_plan plan, void* psi, const void* V, double beta, double lambda, double dt, int nsteps,
              void* stream) {
-  DDI_TRY(ddi::check_gpe(plan, psi, V));
-  if (nsteps < 0 || !ddi::finite_params({beta, lambda, dt})) {
-    ddi::set_error("nsteps must be >= 0 and beta, lambda, dt finite");
-    return DDI_ERR_ARG;
-  }
-  if (nsteps == 0) return DDI_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (plan->p.prec == DDI_FP64) {
-    Gpe<double> g(plan->p, s);
-    return g.step(static_cast<double2*>(psi), static_cast<const double*>(V), beta, lambda, dt, nsteps);
-  }
-  Gpe<float> g(plan->p, s);
-  return g.step(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, dt, nsteps);
+  return ddi::guarded("gpe_step", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, psi, V));
+    if (nsteps < 0 || !ddi::finite_params({beta, lambda, dt})) {
+      ddi::set_error("nsteps must be >= 0 and beta, lambda, dt finite");
+      return DDI_ERR_ARG;
+    }
+    if (nsteps == 0) return DDI_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.step(static_cast<double2*>(psi), static_cast<const double*>(V), beta, lambda, dt, nsteps);
+    }
+    Gpe<float> g(plan->p, s);
+    return g.step(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, dt, nsteps);
+  });
 }
 
 int gpe_step_ex(ddi_plan plan, void* psi, const void* V, double beta, double lambda, const gpe_nonlinearity* nl,
                 double dt, int nsteps, void* stream) {
-  DDI_TRY(ddi::check_gpe(plan, psi, V));
-  if (!nl || nsteps < 0 || !ddi::finite_params({beta, lambda, dt, nl->sigma, nl->delta, nl->q}) ||
-      !(nl->sigma > 0.0) || nl->damping < GPE_DAMP_NONE || nl->damping > GPE_DAMP_POWER ||
-      (nl->damping != GPE_DAMP_NONE && !(nl->delta > 0.0)) || (nl->damping == GPE_DAMP_POWER && !(nl->q > 0.0))) {
-    ddi::set_error("gpe_step_ex: nl must not be NULL, nsteps >= 0, parameters finite, sigma > 0, damping one of "
-                   "GPE_DAMP_*, delta > 0 when damped, q > 0 for GPE_DAMP_POWER");
-    return DDI_ERR_ARG;
-  }
-  if (nsteps == 0) return DDI_OK;
-  ddi::NonlinParams np{nl->sigma, nl->delta, nl->q, nl->damping, 0.0, 0.0};
-  if (nl->damping == GPE_DAMP_LINEAR) {
-    np.c2_h = -std::expm1(-2.0 * nl->delta * nl->sigma * dt) / (2.0 * nl->delta * nl->sigma);
-    np.c2_g = -std::expm1(-2.0 * nl->delta * dt) / (2.0 * nl->delta);
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (plan->p.prec == DDI_FP64) {
-    Gpe<double> g(plan->p, s);
-    return g.step_general(static_cast<double2*>(psi), static_cast<const double*>(V), beta, lambda, np, dt, nsteps);
-  }
-  Gpe<float> g(plan->p, s);
-  return g.step_general(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, np, dt, nsteps);
+  return ddi::guarded("gpe_step_ex", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, psi, V));
+    if (!nl || nsteps < 0 || !ddi::finite_params({beta, lambda, dt, nl->sigma, nl->delta, nl->q}) ||
+        !(nl->sigma > 0.0) || nl->damping < GPE_DAMP_NONE || nl->damping > GPE_DAMP_POWER ||
+        (nl->damping != GPE_DAMP_NONE && !(nl->delta > 0.0)) || (nl->damping == GPE_DAMP_POWER && !(nl->q > 0.0))) {
+      ddi::set_error("gpe_step_ex: nl must not be NULL, nsteps >= 0, parameters finite, sigma > 0, damping one of "
+                     "GPE_DAMP_*, delta > 0 when damped, q > 0 for GPE_DAMP_POWER");
+      return DDI_ERR_ARG;
+    }
+    if (nsteps == 0) return DDI_OK;
+    ddi::NonlinParams np{nl->sigma, nl->delta, nl->q, nl->damping, 0.0, 0.0};
+    if (nl->damping == GPE_DAMP_LINEAR) {
+      np.c2_h = -std::expm1(-2.0 * nl->delta * nl->sigma * dt) / (2.0 * nl->delta * nl->sigma);
+      np.c2_g = -std::expm1(-2.0 * nl->delta * dt) / (2.0 * nl->delta);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.step_general(static_cast<double2*>(psi), static_cast<const double*>(V), beta, lambda, np, dt, nsteps);
+    }
+    Gpe<float> g(plan->p, s);
+    return g.step_general(static_cast<float2*>(psi), static_cast<const float*>(V), beta, lambda, np, dt, nsteps);
+  });
 }
 
 int gpe_energy(ddi_plan plan, const void* psi, const void* V, double beta, double lambda, gpe_stats* out,
                void* stream) {
-  DDI_TRY(ddi::check_gpe(plan, psi, V));
-  if (!out || !ddi::finite_params({beta, lambda})) {
-    ddi::set_error("out must not be NULL and beta, lambda finite");
-    return DDI_ERR_ARG;
-  }
-  memset(out, 0, sizeof *out);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (plan->p.prec == DDI_FP64) {
-    Gpe<double> g(plan->p, s);
-    return g.energy(static_cast<const double2*>(psi), static_cast<const double*>(V), beta, lambda, out);
-  }
-  Gpe<float> g(plan->p, s);
-  return g.energy(static_cast<const float2*>(psi), static_cast<const float*>(V), beta, lambda, out);
+  return ddi::guarded("gpe_energy", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, psi, V));
+    if (!out || !ddi::finite_params({beta, lambda})) {
+      ddi::set_error("out must not be NULL and beta, lambda finite");
+      return DDI_ERR_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.energy(static_cast<const double2*>(psi), static_cast<const double*>(V), beta, lambda, out);
+    }
+    Gpe<float> g(plan->p, s);
+    return g.energy(static_cast<const float2*>(psi), static_cast<const float*>(V), beta, lambda, out);
+  });
 }
 
 int gpe_ground_state(ddi_plan plan, void* phi, const void* V, double beta, double lambda, double dt, double tol,
                      int rule, double inner_tol, int max_steps, int check_every, gpe_stats* out, void* stream) {
-  DDI_TRY(ddi::check_gpe(plan, phi, V));
-  if (!out || !(dt > 0.0) || !(tol > 0.0) || !(inner_tol > 0.0) || max_steps < 1 ||
-      (rule != GPE_STOP_ENERGY && rule != GPE_STOP_PAPER) || !ddi::finite_params({beta, lambda, dt, tol})) {
-    ddi::set_error("invalid gradient-flow arguments (dt, tol, inner_tol > 0; max_steps >= 1; rule 0/1)");
-    return DDI_ERR_ARG;
-  }
-  memset(out, 0, sizeof *out);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (plan->p.prec == DDI_FP64) {
-    Gpe<double> g(plan->p, s);
-    return g.ground_state(static_cast<double2*>(phi), static_cast<const double*>(V), beta, lambda, dt, tol, rule,
+  return ddi::guarded("gpe_ground_state", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, phi, V));
+    if (!out || !(dt > 0.0) || !(tol > 0.0) || !(inner_tol > 0.0) || max_steps < 1 ||
+        (rule != GPE_STOP_ENERGY && rule != GPE_STOP_PAPER) || !ddi::finite_params({beta, lambda, dt, tol})) {
+      ddi::set_error("invalid gradient-flow arguments (dt, tol, inner_tol > 0; max_steps >= 1; rule 0/1)");
+      return DDI_ERR_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.ground_state(static_cast<double2*>(phi), static_cast<const double*>(V), beta, lambda, dt, tol, rule,
+                            inner_tol, max_steps, check_every, out);
+    }
+    Gpe<float> g(plan->p, s);
+    return g.ground_state(static_cast<float2*>(phi), static_cast<const float*>(V), beta, lambda, dt, tol, rule,
                           inner_tol, max_steps, check_every, out);
-  }
-  Gpe<float> g(plan->p, s);
-  return g.ground_state(static_cast<float2*>(phi), static_cast<const float*>(V), beta, lambda, dt, tol, rule,
-                        inner_tol, max_steps, check_every, out);
+  });
 }
 
 int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V, const void* V, double beta,
                      double lambda, double dt, void* stream) {
-  DDI_TRY(ddi::check_gpe(plan, psi_in, cot));
-  DDI_TRY(ddi::check_gpe(plan, grad_V, V));
-  if (!ddi::finite_params({beta, lambda, dt})) {
-    ddi::set_error("beta, lambda, dt must be finite");
-    return DDI_ERR_ARG;
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (plan->p.prec == DDI_FP64) {
-    Gpe<double> g(plan->p, s);
-    return g.adjoint(static_cast<const double2*>(psi_in), static_cast<double2*>(cot), static_cast<double*>(grad_V),
-                     static_cast<const double*>(V), beta, lambda, dt);
-  }
-  Gpe<float> g(plan->p, s);
-  return g.adjoint(static_cast<const float2*>(psi_in), static_cast<float2*>(cot), static_cast<float*>(grad_V),
-                   static_cast<const float*>(V), beta, lambda, dt);
+  return ddi::guarded("gpe_step_adjoint", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, psi_in, cot));
+    DDI_TRY(ddi::check_gpe(plan, grad_V, V));
+    if (!ddi::finite_params({beta, lambda, dt})) {
+      ddi::set_error("beta, lambda, dt must be finite");
+      return DDI_ERR_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.adjoint(static_cast<const double2*>(psi_in), static_cast<double2*>(cot), static_cast<double*>(grad_V),
+                       static_cast<const double*>(V), beta, lambda, dt);
+    }
+    Gpe<float> g(plan->p, s);
+    return g.adjoint(static_cast<const float2*>(psi_in), static_cast<float2*>(cot), static_cast<float*>(grad_V),
+                     static_cast<const float*>(V), beta, lambda, dt);
+  });
 }
 
 }  // extern "C"

@@ -19,18 +19,18 @@
 namespace ddi {
 
 // ---- error reporting -----------------------------------------------------------------
+// a fixed per-thread buffer: recording an error allocates nothing, so it is safe where
+// memory has run out
 namespace {
-thread_local std::string g_err;
+thread_local char g_err[1024] = "";
 }
 void set_error(const char* fmt, ...) {
-  char buf[1024];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
   va_end(ap);
-  g_err = buf;
 }
-const char* last_error() { return g_err.c_str(); }
+const char* last_error() { return g_err; }
 
 namespace {
 
@@ -493,6 +493,7 @@ const char* ddi_status_str(int status) {
     case DDI_ERR_NONFINITE: return "DDI_ERR_NONFINITE: NaN or Inf encountered";
     case DDI_ERR_TIMEOUT: return "DDI_ERR_TIMEOUT: bounded device wait gave up";
     case DDI_ERR_NOCONV: return "DDI_ERR_NOCONV: iteration limit reached";
+    case DDI_ERR_INTERNAL: return "DDI_ERR_INTERNAL: unexpected host-side failure";
     default: return "unknown ddi status";
   }
 }
@@ -500,51 +501,62 @@ const char* ddi_status_str(int status) {
 const char* ddi_last_error(void) { return ddi::last_error(); }
 
 int ddi_quadrature_tables(const ddi_plan_desc* desc, int64_t* M, double* k, double* W, int32_t* l0) {
-  ddi_plan_desc d;
-  std::string err;
-  int s = ddi::normalise_desc(desc, &d, &err);
-  if (s != DDI_OK) {
-    ddi::set_error("%s", err.c_str());
-    return s;
-  }
-  if (!M) {
-    ddi::set_error("M must not be NULL");
-    return DDI_ERR_ARG;
-  }
-  ddi::QuadTables t;
-  ddi::build_quadrature(d, &t);
-  *M = t.M;
-  if (k) memcpy(k, t.k.data(), sizeof(double) * t.k.size());
-  if (W) memcpy(W, t.W.data(), sizeof(double) * t.W.size());
-  if (l0) {
-    const int w = ddi::kernel_width(d);
-    for (int64_t q = 0; q < t.M; ++q)
-      for (int a = 0; a < d.dim; ++a)
-        l0[d.dim * q + a] = (int32_t)ddi::fine_start(t.k[d.dim * q + a], t.h[a], 2 * d.n[a], w);
-  }
-  return DDI_OK;
+  return ddi::guarded("ddi_quadrature_tables", [&]() -> int {
+    ddi_plan_desc d;
+    std::string err;
+    int s = ddi::normalise_desc(desc, &d, &err);
+    if (s != DDI_OK) {
+      ddi::set_error("%s", err.c_str());
+      return s;
+    }
+    if (!M) {
+      ddi::set_error("M must not be NULL");
+      return DDI_ERR_ARG;
+    }
+    ddi::QuadTables t;
+    ddi::build_quadrature(d, &t);
+    *M = t.M;
+    if (k) memcpy(k, t.k.data(), sizeof(double) * t.k.size());
+    if (W) memcpy(W, t.W.data(), sizeof(double) * t.W.size());
+    if (l0) {
+      const int w = ddi::kernel_width(d);
+      for (int64_t q = 0; q < t.M; ++q)
+        for (int a = 0; a < d.dim; ++a)
+          l0[d.dim * q + a] = (int32_t)ddi::fine_start(t.k[d.dim * q + a], t.h[a], 2 * d.n[a], w);
+    }
+    return DDI_OK;
+  });
 }
 
 int ddi_plan_create(ddi_plan* out, const ddi_plan_desc* desc, void* stream) {
-  if (!out) {
-    ddi::set_error("out is NULL");
-    return DDI_ERR_ARG;
-  }
-  *out = nullptr;
-  ddi_plan_s* h = new (std::nothrow) ddi_plan_s();
-  if (!h) {
-    ddi::set_error("host allocation failed");
-    return DDI_ERR_OOM;
-  }
-  int s = ddi::create_plan(h->p, desc, static_cast<cudaStream_t>(stream));
-  if (s == DDI_OK && desc->tile[0] < 0) s = ddi::tune_spread_tile(h->p, static_cast<cudaStream_t>(stream));
-  if (s != DDI_OK) {
-    ddi::destroy_plan(h->p);
-    delete h;
-    return s;
-  }
-  *out = h;
-  return DDI_OK;
+  return ddi::guarded("ddi_plan_create", [&]() -> int {
+    if (!out) {
+      ddi::set_error("out is NULL");
+      return DDI_ERR_ARG;
+    }
+    *out = nullptr;
+    ddi_plan_s* h = new (std::nothrow) ddi_plan_s();
+    if (!h) {
+      ddi::set_error("host allocation failed");
+      return DDI_ERR_OOM;
+    }
+    int s;
+    try {
+      s = ddi::create_plan(h->p, desc, static_cast<cudaStream_t>(stream));
+      if (s == DDI_OK && desc->tile[0] < 0) s = ddi::tune_spread_tile(h->p, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+      ddi::destroy_plan(h->p);  // what was allocated before the failure
+      delete h;
+      throw;
+    }
+    if (s != DDI_OK) {
+      ddi::destroy_plan(h->p);
+      delete h;
+      return s;
+    }
+    *out = h;
+    return DDI_OK;
+  });
 }
 
 int ddi_plan_destroy(ddi_plan plan) {
@@ -564,20 +576,24 @@ int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info) {
 }
 
 int ddi_plan_set_axes(ddi_plan plan, const double* axis_n, const double* axis_m, void* stream) {
-  if (!plan || !axis_n) {
-    ddi::set_error("ddi_plan_set_axes: plan and axis_n must not be NULL");
-    return DDI_ERR_ARG;
-  }
-  return ddi::set_axes(plan->p, axis_n, axis_m, static_cast<cudaStream_t>(stream));
+  return ddi::guarded("ddi_plan_set_axes", [&]() -> int {
+    if (!plan || !axis_n) {
+      ddi::set_error("ddi_plan_set_axes: plan and axis_n must not be NULL");
+      return DDI_ERR_ARG;
+    }
+    return ddi::set_axes(plan->p, axis_n, axis_m, static_cast<cudaStream_t>(stream));
+  });
 }
 
 int ddi_plan_node_order(ddi_plan plan, int64_t* q) {
-  if (!plan || !q) {
-    ddi::set_error("plan and q must not be NULL");
-    return DDI_ERR_ARG;
-  }
-  memcpy(q, plan->p.order.data(), sizeof(int64_t) * plan->p.order.size());
-  return DDI_OK;
+  return ddi::guarded("ddi_plan_node_order", [&]() -> int {
+    if (!plan || !q) {
+      ddi::set_error("plan and q must not be NULL");
+      return DDI_ERR_ARG;
+    }
+    memcpy(q, plan->p.order.data(), sizeof(int64_t) * plan->p.order.size());
+    return DDI_OK;
+  });
 }
 
 static int check_plan_ptrs(ddi_plan plan, const void* a, const void* b) {
@@ -594,82 +610,92 @@ static int check_plan_ptrs(ddi_plan plan, const void* a, const void* b) {
 }
 
 int ddi_apply(ddi_plan plan, const void* rho, void* phi, void* stream) {
-  DDI_TRY(check_plan_ptrs(plan, rho, phi));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Plan& p = plan->p;
-  if (p.prec == DDI_FP64) return ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s);
-  return ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+  return ddi::guarded("ddi_apply", [&]() -> int {
+    DDI_TRY(check_plan_ptrs(plan, rho, phi));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan& p = plan->p;
+    if (p.prec == DDI_FP64) return ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s);
+    return ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+  });
 }
 
 int ddi_apply_host(ddi_plan plan, const void* rho_host, void* phi_host, void* stream) {
-  DDI_TRY(check_plan_ptrs(plan, rho_host, phi_host));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Plan& p = plan->p;
-  const size_t bytes = p.real_size() * (size_t)p.grid_points();
-  DDI_CUDA(cudaMemcpyAsync(p.d_io_in, rho_host, bytes, cudaMemcpyHostToDevice, s));
-  if (p.prec == DDI_FP64) {
-    DDI_TRY(ddi::run_ddi<double>(p, static_cast<const double*>(p.d_io_in), static_cast<double*>(p.d_io_out), s));
-  } else {
-    DDI_TRY(ddi::run_ddi<float>(p, static_cast<const float*>(p.d_io_in), static_cast<float*>(p.d_io_out), s));
-  }
-  DDI_CUDA(cudaMemcpyAsync(phi_host, p.d_io_out, bytes, cudaMemcpyDeviceToHost, s));
-  DDI_CUDA(cudaStreamSynchronize(s));
-  return DDI_OK;
+  return ddi::guarded("ddi_apply_host", [&]() -> int {
+    DDI_TRY(check_plan_ptrs(plan, rho_host, phi_host));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan& p = plan->p;
+    const size_t bytes = p.real_size() * (size_t)p.grid_points();
+    DDI_CUDA(cudaMemcpyAsync(p.d_io_in, rho_host, bytes, cudaMemcpyHostToDevice, s));
+    if (p.prec == DDI_FP64) {
+      DDI_TRY(ddi::run_ddi<double>(p, static_cast<const double*>(p.d_io_in), static_cast<double*>(p.d_io_out), s));
+    } else {
+      DDI_TRY(ddi::run_ddi<float>(p, static_cast<const float*>(p.d_io_in), static_cast<float*>(p.d_io_out), s));
+    }
+    DDI_CUDA(cudaMemcpyAsync(phi_host, p.d_io_out, bytes, cudaMemcpyDeviceToHost, s));
+    DDI_CUDA(cudaStreamSynchronize(s));
+    return DDI_OK;
+  });
 }
 
 int ddi_apply_timed(ddi_plan plan, const void* rho, void* phi, void* stream, const char** names, double* ms,
                     int cap, int* count) {
-  DDI_TRY(check_plan_ptrs(plan, rho, phi));
-  if (!names || !ms || !count || cap < 1) {
-    ddi::set_error("names, ms and count must not be NULL and cap >= 1");
-    return DDI_ERR_ARG;
-  }
-  Plan& p = plan->p;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!p.ev_created) {
-    for (cudaEvent_t& e : p.mark_ev) DDI_CUDA(cudaEventCreate(&e));
-    p.ev_created = true;
-  }
-  p.timing = true;
-  p.nmarks = 0;
-  DDI_CUDA(cudaEventRecord(p.mark_ev[0], s));
-  int st = p.prec == DDI_FP64
-               ? ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s)
-               : ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
-  p.timing = false;
-  if (st != DDI_OK) return st;
-  DDI_CUDA(cudaStreamSynchronize(s));
-  const int n = p.nmarks < cap ? p.nmarks : cap;
-  for (int i = 0; i < n; ++i) {
-    float t = 0.f;
-    DDI_CUDA(cudaEventElapsedTime(&t, p.mark_ev[i], p.mark_ev[i + 1]));
-    names[i] = p.mark_names[i];
-    ms[i] = (double)t;
-  }
-  *count = n;
-  return DDI_OK;
+  return ddi::guarded("ddi_apply_timed", [&]() -> int {
+    DDI_TRY(check_plan_ptrs(plan, rho, phi));
+    if (!names || !ms || !count || cap < 1) {
+      ddi::set_error("names, ms and count must not be NULL and cap >= 1");
+      return DDI_ERR_ARG;
+    }
+    Plan& p = plan->p;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!p.ev_created) {
+      for (cudaEvent_t& e : p.mark_ev) DDI_CUDA(cudaEventCreate(&e));
+      p.ev_created = true;
+    }
+    p.timing = true;
+    p.nmarks = 0;
+    DDI_CUDA(cudaEventRecord(p.mark_ev[0], s));
+    int st = p.prec == DDI_FP64
+                 ? ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s)
+                 : ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+    p.timing = false;
+    if (st != DDI_OK) return st;
+    DDI_CUDA(cudaStreamSynchronize(s));
+    const int n = p.nmarks < cap ? p.nmarks : cap;
+    for (int i = 0; i < n; ++i) {
+      float t = 0.f;
+      DDI_CUDA(cudaEventElapsedTime(&t, p.mark_ev[i], p.mark_ev[i + 1]));
+      names[i] = p.mark_names[i];
+      ms[i] = (double)t;
+    }
+    *count = n;
+    return DDI_OK;
+  });
 }
 
 int ddi_type2(ddi_plan plan, const void* rho, void* c, void* stream) {
-  DDI_TRY(check_plan_ptrs(plan, rho, c));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Plan& p = plan->p;
-  if (p.prec == DDI_FP64) {
-    DDI_TRY(ddi::run_type2<double>(p, static_cast<const double*>(rho), s));
-  } else {
-    DDI_TRY(ddi::run_type2<float>(p, static_cast<const float*>(rho), s));
-  }
-  DDI_CUDA(cudaMemcpyAsync(c, p.d_c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
-  return DDI_OK;
+  return ddi::guarded("ddi_type2", [&]() -> int {
+    DDI_TRY(check_plan_ptrs(plan, rho, c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan& p = plan->p;
+    if (p.prec == DDI_FP64) {
+      DDI_TRY(ddi::run_type2<double>(p, static_cast<const double*>(rho), s));
+    } else {
+      DDI_TRY(ddi::run_type2<float>(p, static_cast<const float*>(rho), s));
+    }
+    DDI_CUDA(cudaMemcpyAsync(c, p.d_c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
+    return DDI_OK;
+  });
 }
 
 int ddi_type1(ddi_plan plan, const void* c, void* phi, void* stream) {
-  DDI_TRY(check_plan_ptrs(plan, c, phi));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Plan& p = plan->p;
-  DDI_CUDA(cudaMemcpyAsync(p.d_c, c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
-  if (p.prec == DDI_FP64) return ddi::run_type1_from_c<double>(p, static_cast<double*>(phi), s);
-  return ddi::run_type1_from_c<float>(p, static_cast<float*>(phi), s);
+  return ddi::guarded("ddi_type1", [&]() -> int {
+    DDI_TRY(check_plan_ptrs(plan, c, phi));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan& p = plan->p;
+    DDI_CUDA(cudaMemcpyAsync(p.d_c, c, p.cx_size() * p.Mh, cudaMemcpyDeviceToDevice, s));
+    if (p.prec == DDI_FP64) return ddi::run_type1_from_c<double>(p, static_cast<double*>(phi), s);
+    return ddi::run_type1_from_c<float>(p, static_cast<float*>(phi), s);
+  });
 }
 
 }  // extern "C"

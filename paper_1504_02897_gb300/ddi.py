@@ -21,7 +21,7 @@ STOP_ENERGY = 0
 STOP_PAPER = 1
 
 _STATUS = {0: "DDI_OK", -1: "DDI_ERR_ARG", -2: "DDI_ERR_CUDA", -3: "DDI_ERR_OOM",
-           -4: "DDI_ERR_NONFINITE", -5: "DDI_ERR_TIMEOUT", -6: "DDI_ERR_NOCONV"}
+           -4: "DDI_ERR_NONFINITE", -5: "DDI_ERR_TIMEOUT", -6: "DDI_ERR_NOCONV", -7: "DDI_ERR_INTERNAL"}
 
 
 class DDIError(RuntimeError):

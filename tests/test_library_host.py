@@ -41,8 +41,8 @@ def test_exports_every_declared_symbol(lib):
 
 def test_status_strings(lib):
     L = lib.load()
-    for s in (0, -1, -2, -3, -4, -5, -6):
-        assert L.ddi_status_str(s)
+    for s in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert L.ddi_status_str(s) and b"unknown" not in L.ddi_status_str(s)
 
 
 CASES = [

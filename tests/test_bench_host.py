@@ -55,3 +55,30 @@ def test_single_process_rate():
     import bench
     assert bench.max_over_ranks(1.5) == 1.5
     assert bench.weak_scaling_rate(40, 1, 0.02) == pytest.approx(2000.0)
+
+
+def test_kernel_byte_model():
+    # the roofline's algorithmic bytes: the split plan's smooth-part passes count as their
+    # NUFFT counterparts, the accumulating crop also reads phi, and the interpolation's
+    # gathered cells follow the quadrature radius (N fine cells for the full rule)
+    sys.path.insert(0, ROOT)
+    import math
+    import bench
+
+    class Info:
+        nodes_used = 49152
+        width = 8
+        kmax = math.pi / (2 * bench.L / bench.N)
+
+    n3 = bench.N ** 3
+    for smooth, base in (("smooth_pad_fft_x", "pad_fft_x"), ("smooth_fft_z_symbol", "fft_z_fwd"),
+                         ("smooth_fft_x_inv_crop", "fft_x_inv_crop")):
+        assert bench.kernel_bytes(smooth, Info) == bench.kernel_bytes(base, Info) > 0
+    assert bench.kernel_bytes("fft_x_inv_crop_add", Info) == bench.kernel_bytes("fft_x_inv_crop", Info) + 4 * n3
+    full = bench.kernel_bytes("interp", Info)
+    ball = int(4.0 / 3.0 * math.pi * (bench.N + 4.0) ** 3) * 8
+    assert full == ball + 49152 * (8 + 16) + 49152 * 8
+    Info.kmax = 2.4
+    # radius 2.4 (2L / pi) = 18.3 fine cells: the gathered ball shrinks by (22.3 / 132)^3
+    assert bench.kernel_bytes("interp", Info) == int(4.0 / 3.0 * math.pi * (2.4 * 2 * bench.L / math.pi + 4.0) ** 3) * 8 + 49152 * 32
+    assert bench.kernel_bytes("no_such_kernel", Info) == 0

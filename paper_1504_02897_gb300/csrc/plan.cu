@@ -9,6 +9,7 @@
 // tile plane, long ones cut into pieces that write partial planes), and all
 // device workspace.  ddi_plan_create is the only call that allocates.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -175,6 +176,11 @@ int build_spread(Plan& p, cudaStream_t stream) {
     total += (long long)L.size();
   }
   p.visits = total;
+  if (total > (long long)INT32_MAX - 1) {
+    // visit ranges are 32-bit on the device
+    set_error("%lld spread visits exceed the 32-bit visit lists; use fewer quadrature nodes", total);
+    return DDI_ERR_ARG;
+  }
   // 2D: one unit per tile (the whole tile is the plane); 3D: one per z-plane
   const bool wrap_owned = dim == 3 ? p.ntile[2] == 1 : true;
   std::vector<int4> visits;

@@ -274,6 +274,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true",
+                    help="ddi3d_128: skip the split-algorithm side measurement (a child process)")
     ap.add_argument("--workload", default="ddi3d_128",
                     choices=["ddi3d_128", "ddi3d_128_split", "batch2d_96", "tsfp128", "gs128", "grad128"],
                     help="ddi3d_128: the headline 3D workload; ddi3d_128_split: the same density by the "
@@ -431,6 +433,10 @@ def main():
                "sample": f"{detail['sample_nodes']} of {N * 64 * 128} nodes (type 2 + type 1 over the full 128^3 "
                          f"grid) in {detail['sample_seconds']:.1f} s, scaled by nodes"}
 
+    split_side = None
+    if rank == 0 and world == 1 and not args.no_split:
+        split_side = split_side_run()
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -455,9 +461,39 @@ def main():
         }
         if cpu:
             out["cpu_baseline"] = cpu
+        if split_side is not None:
+            out["split_algorithm"] = split_side
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def split_side_run(timeout_s=420):
+    """The same density by the split algorithm (``--workload ddi3d_128_split``), measured by a
+    child process after the headline measurement: its own CUDA context, so nothing it does
+    can touch the numbers above.  Returns the child's figures, or the reason it has none."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "ddi3d_128_split", "--steps", "20",
+           "--warmup", "3"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"no result within {timeout_s} s"}
+    if r.returncode != 0:
+        return {"error": f"exit status {r.returncode}: " + " | ".join(r.stderr.strip().splitlines()[-3:])}
+    for line in reversed(r.stdout.strip().splitlines()):
+        try:
+            d = json.loads(line)
+        except ValueError:
+            continue
+        cfg = d["config"]
+        return {"metric": d["metric"], "value": d["value"], "unit": d["unit"], "steps": d["steps"],
+                "ms_per_step": d["ms_per_step"], "fp32_rel_err_vs_fp64": cfg["fp32_rel_err_vs_fp64"],
+                "split_vs_spherical_rule_rel_diff": cfg["split_vs_spherical_rule_rel_diff"],
+                "split_vs_spherical_rule_rel_diff_inner_half_box": cfg["split_vs_spherical_rule_rel_diff_inner_half_box"],
+                "workload": cfg["workload"], "nodes": cfg["nodes"], "roofline": d["roofline"],
+                "ddi_roofline": d["ddi_roofline"], "kernel_ms": d["kernel_ms"], "e2e": d["e2e"],
+                "gpu_launches": d["gpu_launches"], "clocks": d["clocks"]}
+    return {"error": "no JSON line in the child's output"}
 
 
 def _timed_steps(torch, stream, flush, steps, fn):

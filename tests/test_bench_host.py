@@ -82,3 +82,14 @@ def test_kernel_byte_model():
     # radius 2.4 (2L / pi) = 18.3 fine cells: the gathered ball shrinks by (22.3 / 132)^3
     assert bench.kernel_bytes("interp", Info) == int(4.0 / 3.0 * math.pi * (2.4 * 2 * bench.L / math.pi + 4.0) ** 3) * 8 + 49152 * 32
     assert bench.kernel_bytes("no_such_kernel", Info) == 0
+
+
+def test_split_side_run_reports_failure_instead_of_raising():
+    # without a GPU the child process fails; the headline line then carries the reason
+    sys.path.insert(0, ROOT)
+    import torch
+    import bench
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU")
+    res = bench.split_side_run(timeout_s=300)
+    assert set(res) == {"error"} and res["error"]

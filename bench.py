@@ -468,7 +468,7 @@ def main():
         dist.destroy_process_group()
 
 
-def split_side_run(timeout_s=420):
+def split_side_run(timeout_s=240):
     """The same density by the split algorithm (``--workload ddi3d_128_split``), measured by a
     child process after the headline measurement: its own CUDA context, so nothing it does
     can touch the numbers above.  Returns the child's figures, or the reason it has none."""

@@ -116,6 +116,16 @@ def tsfp_step_general(grid, psi, V, beta, lam, dt, ddi, sigma=1.0, damping=0, de
     return kinetic_half(grid, psi2, dt)
 
 
+def tsfp_run_general(grid, psi, coeffs, t0, dt, nsteps, ddi, sigma=1.0, damping=0, delta=0.0, q=1.0):
+    """Strang steps with time-dependent V, beta, lambda (Sec. 5, e.g. Example dy_app_damp):
+    coeffs(t) -> (V, beta, lambda), frozen over each step at its midpoint t0 + (k + 1/2) dt,
+    which keeps the splitting second order where the coefficients are smooth in t."""
+    for k in range(nsteps):
+        V, beta, lam = coeffs(t0 + (k + 0.5) * dt)
+        psi = tsfp_step_general(grid, psi, V, beta, lam, dt, ddi, sigma, damping, delta, q)
+    return psi
+
+
 def energies(grid, phi, V, beta, lam, ddi):
     """Energy split of Sec. 3.2: E_kin, E_pot, E_int, E_dip, E, mu, virial I, mass."""
     ax = tuple(range(grid.dim))

@@ -302,6 +302,15 @@ class Plan:
                "gpe_step_ex")
         return psi
 
+    def gpe_run(self, psi, coeffs, t0, dt, nsteps, sigma=1.0, damping=DAMP_NONE, delta=0.0, q=1.0, stream=None):
+        """Strang steps with time-dependent trap and coefficients (Sec. 5, e.g. the collapse
+        example): coeffs(t) returns (V, beta, lambda), V a device tensor of the plan, and is
+        evaluated at each step's midpoint t0 + (k + 1/2) dt; each step is one gpe_step_ex."""
+        for k in range(int(nsteps)):
+            V, beta, lam = coeffs(t0 + (k + 0.5) * dt)
+            self.gpe_step_ex(psi, V, beta, lam, dt, 1, sigma, damping, delta, q, stream)
+        return psi
+
     def gpe_energy(self, psi, V, beta, lam, stream=None):
         st = GpeStats()
         _check(load().gpe_energy(self._h, self._req(psi, True), self._req(V), float(beta), float(lam),

@@ -18,6 +18,8 @@ Recipes (the paper uses analytic Gaussians and GPE states, no dataset):
   N(0,1) cosine/sine coefficients scaled to max |eta| = 1; discrete mass 1.
 * trap_directions: white noise N(0,1) smoothed by a Gaussian of width 2h (periodic),
   scaled to max |d| = 1.
+* collapse_schedule: the time-dependent trap switch, beta(t) and lambda(t) of the
+  collapse-and-explosion example of Sec. 5 (Example dy_app_damp).
 """
 import math
 
@@ -132,3 +134,38 @@ def trap_directions(n, count=16, seed=0):
         d = ndimage.gaussian_filter(rng.standard_normal(shape), sigma=2.0, mode="wrap")
         out.append(d / np.max(np.abs(d)))
     return out
+
+
+COLLAPSE_GAMMAS = (1.65, 1.0, 1.325)   # trap frequencies of Example dy_app_damp
+COLLAPSE_BETA0 = 761.102
+
+
+def collapse_b(t):
+    """b(t) of Example dy_app_damp (t in [0, 1.2]), continuous at t = 0.4."""
+    if t <= 0.4:
+        return (-125.0 * t - 25.0 * math.exp(-5.0 * t) + 215.0) / 133.0
+    return (25.0 * (1.0 - math.exp(-2.0)) * math.exp(-6.25 * t + 2.5) + 140.0) / 133.0
+
+
+def collapse_schedule(t, t_hold=0.2):
+    """(trap on, beta, lambda) at time t for Example dy_app_damp: the trap
+    (gamma_x, gamma_y, gamma_z) = (1.65, 1, 1.325) is on for t <= 4 + t_hold, lambda = 82.864
+    for t <= 5.6 + t_hold, and beta = 761.102 (1 + 28 / (75 t - 280)) on [0, 3.2], 761.102 * 0.3
+    on [3.2, 3.6], 761.102 (1 - 1 / b(t - 3.6)) on [3.6, 4.8] and 38.8066 on [4.8, 5.6 + t_hold],
+    then 0.  Reading: the printed formula multiplies every branch by 761.102, but the last
+    nonzero branch is the value the third branch reaches at t = 4.8 (761.102 (1 - 1/b(1.2)) =
+    38.807), so 38.8066 is beta itself, not a factor."""
+    trap = t <= 4.0 + t_hold
+    lam = 82.864 if t <= 5.6 + t_hold else 0.0
+    if t <= 3.2:
+        beta = COLLAPSE_BETA0 * (1.0 + 28.0 / (75.0 * t - 280.0))
+    elif t <= 3.6:
+        beta = COLLAPSE_BETA0 * 0.3
+    elif t <= 4.8:
+        beta = COLLAPSE_BETA0 * (1.0 - 1.0 / collapse_b(t - 3.6))
+    elif t <= 5.6 + t_hold:
+        beta = 38.8066
+    else:
+        beta = 0.0
+    return trap, beta, lam
+

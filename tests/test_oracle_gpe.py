@@ -252,3 +252,42 @@ def test_tangent_linear_model_matches_finite_differences():
     fd = (fwd(eps) - fwd(-eps)) / (2 * eps)
     tl = gpe.tsfp_tangent(grid, psi0, V, beta, lam, dt, nsteps, ddi, dpsi, dV)
     assert np.max(np.abs(fd - tl)) <= 1e-7 * np.max(np.abs(tl))
+
+
+def test_time_dependent_run_is_second_order():
+    # coefficients frozen at each step's midpoint keep Strang splitting second order for smooth
+    # beta(t), lambda(t) (here with three-body loss, Case III); freezing them at the step's
+    # start (the same run with the schedule shifted by dt/2) is only first order
+    grid, ddi, n, lo, ln = _setup(16, 8.0)
+    X, Y, Z = synth.coords(n, lo, ln)
+    V = 0.5 * (X ** 2 + Y ** 2 + Z ** 2)
+    psi0 = (math.pi ** -0.75) * np.exp(-0.5 * (X ** 2 + Y ** 2 + Z ** 2)).astype(complex)
+
+    def coeffs(t):
+        beta = 2.0 * (1.0 + 0.5 * math.sin(10.0 * t))
+        return V, beta, 0.5 * beta
+
+    def run(dt, shift):
+        return gpe.tsfp_run_general(grid, psi0, lambda t: coeffs(t - shift * dt), 0.0, dt, int(round(0.28 / dt)),
+                                    ddi, 1.0, 2, 0.5, 2.0)
+
+    for shift, order in ((0.0, 2.0), (0.5, 1.0)):
+        sols = [run(0.008 / 2 ** k, shift) for k in range(3)]
+        d = [np.linalg.norm(sols[k] - sols[k + 1]) for k in range(2)]
+        assert abs(math.log2(d[0] / d[1]) - order) < 0.15, (shift, d)
+
+
+def test_collapse_schedule_is_continuous():
+    # Example dy_app_damp: b(t) and beta(t) are continuous at their breakpoints; the last
+    # nonzero branch is the printed 38.8066 (see synth.collapse_schedule for the reading)
+    eps = 1e-9
+    assert abs(synth.collapse_b(0.4) - synth.collapse_b(0.4 + eps)) < 1e-7
+    for tb in (3.2, 3.6):
+        a, b = synth.collapse_schedule(tb)[1], synth.collapse_schedule(tb + eps)[1]
+        assert abs(a - b) <= 1e-6 * abs(a)
+    assert abs(synth.collapse_schedule(4.8)[1] - 38.8066) <= 1e-4
+    assert synth.collapse_schedule(0.0)[1] == pytest.approx(761.102 * 0.9)
+    assert synth.collapse_schedule(3.4)[1] == pytest.approx(761.102 * 0.3)
+    assert synth.collapse_schedule(4.2)[0] and not synth.collapse_schedule(4.2 + eps)[0]
+    assert synth.collapse_schedule(5.8)[2] == 82.864 and synth.collapse_schedule(5.8 + eps)[2] == 0.0
+    assert synth.collapse_schedule(5.8 + eps)[1] == 0.0

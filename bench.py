@@ -582,10 +582,9 @@ def bench_split(args):
     alg = kernel_bytes(dominant, info)
     achieved = alg / (avg[dominant] * 1e-3) / 1e9
     # the method's bytes: rho in, phi out and the smooth part's four sweeps of the padded
-    # grid (write after the pad, one FFT pass, read by the crop); the ball's part costs O(1)
-    # in the method but runs through the fine grid here (its six passes are counted apart)
+    # grid (write after the pad, one FFT pass, read by the crop); the ball's part is O(1) in the
+    # method (here: its x passes, the spread's write of the fine grid and the band passes)
     method_bytes = 8 * N ** 3 + 4 * (2 * N) ** 3 * 8
-    impl_bytes = method_bytes + 4 * (2 * N) ** 3 * 8
 
     host_in = torch.from_numpy(w["rho"].astype(np.float32)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -612,9 +611,8 @@ def bench_split(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": dominant, "kernel_ms": avg[dominant],
                      "peak_source": src + " hbm_gbs (copy)"},
-        "ddi_roofline": {"method_bytes": method_bytes, "implementation_bytes": impl_bytes,
-                         "frac_of_method": method_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
-                         "frac_of_implementation": impl_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+        "ddi_roofline": {"method_bytes": method_bytes,
+                         "frac_of_method": method_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
         "kernel_ms": avg,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N ** 3, "d2h_bytes_per_step": 4 * N ** 3},
         "gpu_launches": launches * args.steps,

@@ -93,6 +93,10 @@ typedef struct {
                           in 2D the symbol's factor |k| = r |e * khat|.  Default polar (3D) / azimuthal
                           (2D) size ceil(N/2 ratio) / 2 ceil(N ratio), ratio = max h / min h.  Not
                           combined with split_k0. */
+  int split_full_passes; /* split plans: 0 => the ball's type-2 / type-1 NUFFT runs its y and z fine-grid
+                          passes only on the lines through its taps (|l_d| <= kmax h_d nf_d / (2 pi) +
+                          w/2 + 2 around k = 0; the other lines are zero or never read); 1 => on
+                          every line, as a plan without split_k0 does */
 } ddi_plan_desc;
 
 /* Read-only facts about a built plan (sizes and the NUFFT parameters chosen). */

@@ -170,6 +170,9 @@ struct Plan {
   size_t spread_smem = 0;     // launch geometry of the spread (fixed per plan)
   int spread_blocks = 1;
   int nsplit = 0, nslots = 0;
+  // split plans: half-widths of the band of fine-grid lines around k = 0 that hold every tap
+  // of the ball's nodes (x and y; 0 = all lines); the ball's NUFFT passes skip the others
+  int band[2] = {0, 0};
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n} (FP32: n heads, then n tails)
   // GPE workspace

@@ -118,6 +118,59 @@ struct AllZ {
   }
 };
 
+// The band of fine-grid lines around k = 0 that holds every tap of a split plan's ball
+// nodes: index i = 0..2b of the band is fine position i (i <= b) or nf - (2b + 1 - i).
+__host__ __device__ inline int band_line(int i, int b, int nf) { return i <= b ? i : nf - (2 * b + 1 - i); }
+
+// y lines of the planes z in the block, only the x-columns in the band (split plans' ball)
+template <typename T, bool FWD>
+struct BandY {
+  using C = cx_t<T>;
+  static constexpr bool kPreciseTwiddles = false;
+  using Ref = long long;  // fine-grid offset of the line's first element
+  Geo<T> g;
+  int bx;
+  __host__ __device__ long long nlines() const { return (long long)(2 * bx + 1) * g.az.n; }
+  __device__ bool contig() const { return false; }
+  __device__ Ref ref(long long L) const {
+    const int wx = 2 * bx + 1;
+    return g.fidx(g.az.fine_of((int)(L / wx)), 0, band_line((int)(L % wx), bx, g.ax.nf));
+  }
+  __device__ C load(Ref r, int i) const {
+    if (FWD && !g.ay.in_block(i)) return cmk<C>((T)0, (T)0);
+    return __ldg(g.fine + r + (long long)i * g.ax.nf);
+  }
+  __device__ void store(Ref r, int i, C v) const {
+    if (!FWD && !g.ay.in_block(i)) return;
+    g.fine[r + (long long)i * g.ax.nf] = v;
+  }
+};
+
+// z columns in the band of x and y (split plans' ball)
+template <typename T, bool FWD>
+struct BandZ {
+  using C = cx_t<T>;
+  static constexpr bool kPreciseTwiddles = false;
+  using Ref = long long;  // the column's (y, x) offset
+  Geo<T> g;
+  int bx, by;
+  __host__ __device__ long long nlines() const { return (long long)(2 * bx + 1) * (2 * by + 1); }
+  __device__ bool contig() const { return false; }
+  __device__ Ref ref(long long L) const {
+    const int wx = 2 * bx + 1;
+    const int lx = band_line((int)(L % wx), bx, g.ax.nf), ly = band_line((int)(L / wx), by, g.ay.nf);
+    return (long long)ly * g.ax.nf + lx;
+  }
+  __device__ C load(Ref r, int i) const {
+    if (FWD && !g.az.in_block(i)) return cmk<C>((T)0, (T)0);
+    return __ldg(g.fine + (long long)i * g.ay.nf * g.ax.nf + r);
+  }
+  __device__ void store(Ref r, int i, C v) const {
+    if (!FWD && !g.az.in_block(i)) return;
+    g.fine[(long long)i * g.ay.nf * g.ax.nf + r] = v;
+  }
+};
+
 // inverse x with crop, deconvolution and real part: lines = grid rows (jy, jz); ACC adds
 // the result to phi instead of storing it
 template <typename T, bool ACC>
@@ -222,11 +275,25 @@ Geo<T> geo_of(Plan& p, bool unit = false) {
 
 }  // namespace
 
+// split plans with a band: the ball's taps lie in the x-band (y pass) and the x/y band (z
+// pass), so only those lines are transformed; interpolation reads nothing else
+template <typename T>
+bool use_band(const Plan& p) {
+  return p.dim == 3 && p.band[0] > 0 && p.band[1] > 0;
+}
+
 template <typename T>
 int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t s) {
   const Geo<T> g = geo_of<T>(p);
   DDI_TRY((dispatch_policy<T, -1>(p.nf[0], PadX<T>{g, rho}, twiddles(p, p.nf[0]), s)));
   p.mark("pad_fft_x", s);
+  if (use_band<T>(p)) {
+    DDI_TRY((dispatch_policy<T, -1>(p.nf[1], BandY<T, true>{g, p.band[0]}, twiddles(p, p.nf[1]), s)));
+    p.mark("band_fft_y_fwd", s);
+    DDI_TRY((dispatch_policy<T, -1>(p.nf[2], BandZ<T, true>{g, p.band[0], p.band[1]}, twiddles(p, p.nf[2]), s)));
+    p.mark("band_fft_z_fwd", s);
+    return DDI_OK;
+  }
   DDI_TRY((dispatch_policy<T, -1>(p.nf[1], BlockY<T, true>{g}, twiddles(p, p.nf[1]), s)));
   p.mark("fft_y_fwd", s);
   if (p.dim == 3) {
@@ -239,12 +306,21 @@ int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t s) {
 template <typename T>
 int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s, bool acc) {
   const Geo<T> g = geo_of<T>(p);
-  if (p.dim == 3) {
-    DDI_TRY((dispatch_policy<T, +1>(p.nf[2], AllZ<T, false>{g}, twiddles(p, p.nf[2]), s)));
-    p.mark("fft_z_inv", s);
+  if (use_band<T>(p)) {
+    // the spread wrote every fine cell, zero off the taps, so the skipped lines are zero
+    // before and after their transforms, as the crop expects
+    DDI_TRY((dispatch_policy<T, +1>(p.nf[2], BandZ<T, false>{g, p.band[0], p.band[1]}, twiddles(p, p.nf[2]), s)));
+    p.mark("band_fft_z_inv", s);
+    DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BandY<T, false>{g, p.band[0]}, twiddles(p, p.nf[1]), s)));
+    p.mark("band_fft_y_inv", s);
+  } else {
+    if (p.dim == 3) {
+      DDI_TRY((dispatch_policy<T, +1>(p.nf[2], AllZ<T, false>{g}, twiddles(p, p.nf[2]), s)));
+      p.mark("fft_z_inv", s);
+    }
+    DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BlockY<T, false>{g}, twiddles(p, p.nf[1]), s)));
+    p.mark("fft_y_inv", s);
   }
-  DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BlockY<T, false>{g}, twiddles(p, p.nf[1]), s)));
-  p.mark("fft_y_inv", s);
   if (acc)
     DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T, true>{g, phi}, twiddles(p, p.nf[0]), s)));
   else

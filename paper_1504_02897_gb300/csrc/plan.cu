@@ -272,6 +272,14 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   }
   p.w = kernel_width(d);
   p.beta = kernel_beta(p.w);
+  if (p.split() && !d.split_full_passes) {
+    // every tap l of a node with |k_a| <= kmax lies within |l| <= kmax h nf / (2 pi) + w/2 (first tap
+    // ceil(s - w/2), last tap + w - 1); two cells of margin; no band where it would cover the axis
+    for (int a = 0; a < 2; ++a) {
+      const int b = (int)std::floor(d.kmax * p.h[a] * (double)p.nf[a] / (2.0 * M_PI) + 0.5 * (double)p.w) + 2;
+      p.band[a] = 2 * b + 1 < p.nf[a] ? b : 0;
+    }
+  }
   build_quadrature(d, &p.quad, /*keep_dirs=*/gpe);
   p.M = p.quad.M;
   choose_tile(p);

@@ -135,6 +135,10 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
     if (d.ntheta == 0) d.ntheta = size_for(0.32 * K, 8);
     if (d.nphi == 0) d.nphi = size_for(0.64 * K, 16);
   }
+  if (d.split_full_passes != 0 && d.split_full_passes != 1) {
+    *err = "split_full_passes must be 0 or 1";
+    return DDI_ERR_ARG;
+  }
   if (d.ellipsoid != 0 && d.ellipsoid != 1) {
     *err = "ellipsoid must be 0 or 1";
     return DDI_ERR_ARG;

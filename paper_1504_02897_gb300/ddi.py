@@ -36,7 +36,7 @@ class PlanDesc(ctypes.Structure):
                 ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
                 ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("split_k0", ctypes.c_double),
-                ("ellipsoid", ctypes.c_int)]
+                ("ellipsoid", ctypes.c_int), ("split_full_passes", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -136,12 +136,15 @@ def _check(status, where):
 
 
 def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
-              precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0, ellipsoid=False):
+              precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0, ellipsoid=False,
+              split_full_passes=False):
     """A plan descriptor (``ddi_plan_desc``).  split_k0 != 0 selects the improved split
     algorithm of Sec. 2.1 (Eq. 3.9), 3D only: window q = exp(-|k|^2/k0^2) with k0 = split_k0
     (< 0: the library's default), the quadrature on the small ball |k| <= kmax (0: 6 k0)
     and the smooth part by a zero-padded FFT convolution.  ellipsoid: the quadrature on the
-    ellipsoid |k_d| <= pi / h_d (heterogeneous boxes, e.g. thin domains h_z = eps h_x)."""
+    ellipsoid |k_d| <= pi / h_d (heterogeneous boxes, e.g. thin domains h_z = eps h_x).
+    split_full_passes: a split plan's ball NUFFT transforms every fine-grid line instead of
+    the band around k = 0 that holds its taps (same result; for comparison)."""
     d = PlanDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -161,6 +164,7 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.chunk = int(chunk)
     d.split_k0 = float(split_k0)
     d.ellipsoid = 1 if ellipsoid else 0
+    d.split_full_passes = 1 if split_full_passes else 0
     return d
 
 

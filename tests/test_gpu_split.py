@@ -43,6 +43,13 @@ def _unit(v):
 
 
 def _case(name):
+    if name == "cube64":
+        # h = 1/4: the ball's taps fill about half of each fine axis, so the band skips lines
+        n, lo, ln = synth.box(64, 8.0)
+        X, Y, Z = synth.coords(n, lo, ln)
+        rho = np.exp(-(X ** 2 / 1.5 + Y ** 2 + (Z - 0.5) ** 2 / 2.0))
+        return dict(n=n, lo=lo, ln=ln, rho=rho, axis=_unit((math.sin(0.4), 0.0, math.cos(0.4))), m=None, k0=0.8,
+                    sizes=dict(nr=48, ntheta=32, nphi=64))
     if name == "cube32":
         n, lo, ln = synth.box(32, 8.0)
         X, Y, Z = synth.coords(n, lo, ln)
@@ -58,6 +65,9 @@ def _case(name):
 
 
 def _plan(D, c, precision, **kw):
+    # every line of the fine grid transformed (the band of lines around k = 0 that the ball's
+    # taps need is compared with this at the end of the file)
+    kw.setdefault("split_full_passes", True)
     return D.Plan(3, c["n"], c["lo"], c["ln"], c["axis"], c["m"], precision=precision, split_k0=c["k0"],
                   **c["sizes"], **kw)
 
@@ -117,7 +127,8 @@ def test_split_set_axes_equals_fresh_plan(D):
     a1, m1 = _unit((0.3, -0.5, 0.8)), _unit((0.7, 0.1, -0.2))
     plan.set_axes(a1, m1)
     got = plan.apply(rho)
-    fresh = D.Plan(3, c["n"], c["lo"], c["ln"], a1, m1, precision=1, split_k0=c["k0"], **c["sizes"])
+    fresh = D.Plan(3, c["n"], c["lo"], c["ln"], a1, m1, precision=1, split_k0=c["k0"], split_full_passes=True,
+                   **c["sizes"])
     ref = fresh.apply(rho)
     torch.cuda.synchronize()
     assert torch.equal(got, ref)
@@ -140,11 +151,27 @@ def test_split_time_splitting_step(D):
     ref = psi0
     for _ in range(steps):
         ref = ogpe.tsfp_step(grid, ref, V, beta, lam, dt, ddi)
-    plan = D.Plan(3, n, lo, ln, axis, precision=0, split_k0=k0, **sizes)
+    plan = D.Plan(3, n, lo, ln, axis, precision=0, split_k0=k0, split_full_passes=True, **sizes)
     psi = _t(psi0, plan.cplx_dtype)
     plan.gpe_step(psi, _t(V, plan.real_dtype), beta, lam, dt, steps)
     got = psi.cpu().numpy()
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["cube64", "cube32", "ragged"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_band_equals_full_passes(D, name, precision):
+    # the lines the band skips are zero (spread) or never read (interpolation), and the FFT of
+    # zeros is exactly zero, so the banded plan (the default) computes the same bits
+    import torch
+    c = _case(name)
+    full = _plan(D, c, precision)
+    band = _plan(D, c, precision, split_full_passes=False)
+    rho = _t(c["rho"], full.real_dtype)
+    a = full.apply(rho)
+    b = band.apply(rho)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
 
 
 @pytest.fixture(scope="module")

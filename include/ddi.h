@@ -115,6 +115,9 @@ typedef struct {
   size_t device_bytes; /* device memory held by the plan */
   double spread_tuned_ms; /* spread time of the tile the autotuner picked, in ms; 0 if not tuned */
   double split_k0;     /* window width k0 of the split algorithm; 0 if the plan does not split */
+  int ellipsoid;       /* 1 if the quadrature is the ellipsoidal rule */
+  int band[2];         /* split plans: half-widths (x, y) of the band of fine-grid lines the ball's
+                          y and z passes transform (0, 0: every line) */
 } ddi_plan_info;
 
 /* Energies of Sec. 3.2 for a state phi (all FP64). */
@@ -151,6 +154,12 @@ int ddi_quadrature_tables(const ddi_plan_desc* desc, int64_t* M, double* k, doub
 int ddi_plan_create(ddi_plan* out, const ddi_plan_desc* desc, void* stream);
 int ddi_plan_destroy(ddi_plan plan);
 int ddi_plan_get_info(ddi_plan plan, ddi_plan_info* info);
+/* What ddi_plan_create would build from `desc`, without building it (host only, no GPU
+ * needed): the normalised sizes, fine grid, kernel width and shape, node counts, kmax,
+ * quadrature sizes, split_k0, ellipsoid and band.  Fields that depend on the device build
+ * (tile, spread work items, device_bytes, spread_tuned_ms) are 0.  DDI_ERR_ARG for an invalid
+ * descriptor (as ddi_plan_create) or a NULL info. */
+int ddi_plan_describe(const ddi_plan_desc* desc, ddi_plan_info* info);
 
 /* ---- the DDI (Sec. 2.1) -------------------------------------------------------- */
 /* Phi = U_dip * rho by the quadrature sum above, through the NUFFT: deconvolve and

@@ -272,14 +272,9 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   }
   p.w = kernel_width(d);
   p.beta = kernel_beta(p.w);
-  if (p.split() && !d.split_full_passes) {
-    // every tap l of a node with |k_a| <= kmax lies within |l| <= kmax h nf / (2 pi) + w/2 (first tap
-    // ceil(s - w/2), last tap + w - 1); two cells of margin; no band where it would cover the axis
-    for (int a = 0; a < 2; ++a) {
-      const int b = (int)std::floor(d.kmax * p.h[a] * (double)p.nf[a] / (2.0 * M_PI) + 0.5 * (double)p.w) + 2;
-      p.band[a] = 2 * b + 1 < p.nf[a] ? b : 0;
-    }
-  }
+  // every tap l of a ball node with |k_a| <= kmax lies within |l| <= kmax h nf / (2 pi) + w/2 (first
+  // tap ceil(s - w/2), last tap + w - 1)
+  split_band(d, p.w, p.band);
   build_quadrature(d, &p.quad, /*keep_dirs=*/gpe);
   p.M = p.quad.M;
   choose_tile(p);
@@ -487,6 +482,9 @@ void fill_info(const Plan& p, ddi_plan_info* info) {
   info->device_bytes = p.bytes;
   info->spread_tuned_ms = p.tuned_ms;
   info->split_k0 = p.split() ? p.desc.split_k0 : 0.0;
+  info->ellipsoid = p.desc.ellipsoid;
+  info->band[0] = p.band[0];
+  info->band[1] = p.band[1];
 }
 
 void destroy_plan(Plan& p) { free_plan(p); }
@@ -538,6 +536,41 @@ int ddi_quadrature_tables(const ddi_plan_desc* desc, int64_t* M, double* k, doub
         for (int a = 0; a < d.dim; ++a)
           l0[d.dim * q + a] = (int32_t)ddi::fine_start(t.k[d.dim * q + a], t.h[a], 2 * d.n[a], w);
     }
+    return DDI_OK;
+  });
+}
+
+int ddi_plan_describe(const ddi_plan_desc* desc, ddi_plan_info* info) {
+  return ddi::guarded("ddi_plan_describe", [&]() -> int {
+    if (!info) {
+      ddi::set_error("info must not be NULL");
+      return DDI_ERR_ARG;
+    }
+    ddi_plan_desc d;
+    std::string err;
+    const int s = ddi::normalise_desc(desc, &d, &err);
+    if (s != DDI_OK) {
+      ddi::set_error("%s", err.c_str());
+      return s;
+    }
+    std::memset(info, 0, sizeof *info);
+    info->dim = d.dim;
+    info->precision = d.precision;
+    for (int a = 0; a < 3; ++a) {
+      info->n[a] = a < d.dim ? d.n[a] : 1;
+      info->nf[a] = a < d.dim ? 2 * d.n[a] : 1;
+    }
+    info->width = ddi::kernel_width(d);
+    info->beta = ddi::kernel_beta(info->width);
+    info->nodes = (int64_t)d.nr * d.ntheta * d.nphi;
+    info->nodes_used = info->nodes / 2;
+    info->kmax = d.kmax;
+    info->nr = d.nr;
+    info->ntheta = d.ntheta;
+    info->nphi = d.nphi;
+    info->split_k0 = d.split_k0 > 0.0 ? d.split_k0 : 0.0;
+    info->ellipsoid = d.ellipsoid;
+    ddi::split_band(d, info->width, info->band);
     return DDI_OK;
   });
 }

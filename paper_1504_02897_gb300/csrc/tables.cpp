@@ -368,6 +368,18 @@ int kernel_width(const ddi_plan_desc& d) {
 
 double kernel_beta(int width) { return 2.30 * (double)width; }
 
+void split_band(const ddi_plan_desc& d, int width, int band[2]) {
+  band[0] = band[1] = 0;
+  if (!(d.split_k0 > 0.0) || d.split_full_passes || d.dim != 3) return;
+  for (int a = 0; a < 2; ++a) {
+    const double h = d.len[a] / (double)d.n[a];
+    const int nf = 2 * d.n[a];
+    const int b = (int)std::floor(d.kmax * h * (double)nf / kTwoPi + 0.5 * (double)width) + 2;
+    band[a] = 2 * b + 1 < nf ? b : 0;
+  }
+  if (band[0] == 0 || band[1] == 0) band[0] = band[1] = 0;
+}
+
 int64_t fine_start(double k, double h, int nf, int width) {
   const double scale = (h * (double)nf) / kTwoPi;
   return (int64_t)std::ceil(k * scale - 0.5 * (double)width);

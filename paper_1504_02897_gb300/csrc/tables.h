@@ -40,6 +40,11 @@ double symbol_divisor(int dim);
 int kernel_width(const ddi_plan_desc& d);
 double kernel_beta(int width);
 
+// Split plans: half-widths (x, y) of the band of fine-grid lines around k = 0 that holds
+// every tap of the ball's nodes, |l| <= kmax h nf / (2 pi) + w/2, plus two cells; 0 where the
+// band would cover the axis, and both 0 when the plan does not split or asks for full passes.
+void split_band(const ddi_plan_desc& d, int width, int band[2]);
+
 // First fine-grid tap ceil(k * (h nf / 2pi) - w/2) along one axis.
 int64_t fine_start(double k, double h, int nf, int width);
 

@@ -46,7 +46,8 @@ class PlanInfo(ctypes.Structure):
                 ("spread_items", ctypes.c_int), ("spread_split_tiles", ctypes.c_int),
                 ("interp_items", ctypes.c_int), ("kmax", ctypes.c_double), ("nr", ctypes.c_int),
                 ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
-                ("spread_tuned_ms", ctypes.c_double), ("split_k0", ctypes.c_double)]
+                ("spread_tuned_ms", ctypes.c_double), ("split_k0", ctypes.c_double), ("ellipsoid", ctypes.c_int),
+                ("band", ctypes.c_int * 2)]
 
 
 class GpeNonlinearity(ctypes.Structure):
@@ -71,7 +72,7 @@ EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_pla
            "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
            "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc",
            "ddi_batch_create", "ddi_batch_destroy", "ddi_batch_size", "ddi_batch_get_info", "ddi_batch_apply",
-           "ddi_batch_graph_stats", "ddi_plan_set_axes", "gpe_step_ex"]
+           "ddi_batch_graph_stats", "ddi_plan_set_axes", "gpe_step_ex", "ddi_plan_describe"]
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
@@ -100,6 +101,7 @@ def load():
         "ddi_plan_create": ([ctypes.POINTER(vp), ctypes.POINTER(PlanDesc), vp], ci),
         "ddi_plan_destroy": ([vp], ci),
         "ddi_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], ci),
+        "ddi_plan_describe": ([ctypes.POINTER(PlanDesc), ctypes.POINTER(PlanInfo)], ci),
         "ddi_apply": ([vp, vp, vp, vp], ci),
         "ddi_apply_host": ([vp, vp, vp, vp], ci),
         "ddi_apply_timed": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(cd), ci,
@@ -166,6 +168,13 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.ellipsoid = 1 if ellipsoid else 0
     d.split_full_passes = 1 if split_full_passes else 0
     return d
+
+
+def describe(desc):
+    """PlanInfo of the plan ddi_plan_create would build from desc, without building it (no GPU)."""
+    info = PlanInfo()
+    _check(load().ddi_plan_describe(ctypes.byref(desc), ctypes.byref(info)), "ddi_plan_describe")
+    return info
 
 
 def quadrature_tables(desc):

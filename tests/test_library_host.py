@@ -284,3 +284,39 @@ def test_ellipsoid_descriptor_validation(lib, bad):
     with pytest.raises(lib.DDIError) as e:
         lib.quadrature_tables(desc)
     assert e.value.status == -1
+
+
+# ---- ddi_plan_describe: the plan's derived parameters without a GPU ---------------------------------
+
+def test_describe_matches_the_tables_and_defaults(lib):
+    desc = lib.make_desc(3, (128,) * 3, (-12,) * 3, (24,) * 3, (0.5, 0, math.sqrt(0.75)), precision=1)
+    info = lib.describe(desc)
+    assert (info.nr, info.ntheta, info.nphi) == (128, 64, 128) and info.nodes == 128 * 64 * 128
+    assert info.nodes_used == info.nodes // 2 and list(info.nf) == [256] * 3
+    assert info.width == 8 and info.kmax == pytest.approx(math.pi / 0.1875)
+    assert info.split_k0 == 0.0 and list(info.band) == [0, 0] and info.ellipsoid == 0
+    info64 = lib.describe(lib.make_desc(2, (64, 32), (-8, -4), (16, 8), (1, 0, 0), precision=0, ellipsoid=True))
+    assert info64.width == 14 and info64.ellipsoid == 1 and list(info64.nf) == [128, 64, 1]
+    import ctypes
+    assert lib.load().ddi_plan_describe(ctypes.byref(desc), None) == -1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_band_holds_every_ball_tap(lib, precision):
+    # the band of fine lines the ball's y/z passes transform contains every tap of every node
+    # (first taps from the library's own tables), and is narrower than the axis
+    desc = lib.make_desc(3, (128,) * 3, (-12,) * 3, (24,) * 3, (0.5, 0, math.sqrt(0.75)), precision=precision,
+                         split_k0=-1.0)
+    info = lib.describe(desc)
+    assert list(info.band) == ([27, 27] if precision == 0 else [24, 24])
+    _, _, l0 = lib.quadrature_tables(desc)
+    w = info.width
+    for a in range(2):
+        assert l0[:, a].min() >= -info.band[a] and (l0[:, a] + w - 1).max() <= info.band[a]
+        assert 2 * info.band[a] + 1 < info.nf[a]
+    full = lib.make_desc(3, (128,) * 3, (-12,) * 3, (24,) * 3, (0.5, 0, math.sqrt(0.75)), precision=precision,
+                         split_k0=-1.0, split_full_passes=True)
+    assert list(lib.describe(full).band) == [0, 0]
+    # a band that would cover the axis is not used
+    coarse = lib.make_desc(3, (32,) * 3, (-8,) * 3, (16,) * 3, (0, 0, 1), precision=0, split_k0=0.8)
+    assert list(lib.describe(coarse).band) == [0, 0]

@@ -133,3 +133,19 @@ def test_split_agrees_with_spherical_oracle_where_both_resolve():
     b = nudft.ddi(rho, qd.plan_tables(3, n, ln, nax), n, lo, ln)
     inner = (np.abs(X) <= 3) & (np.abs(Y) <= 3) & (np.abs(Z) <= 3)
     assert np.max(np.abs(a - b)[inner]) <= 1e-10 * np.max(np.abs(a))
+
+
+def test_split_operator_is_symmetric():
+    # <a, Phi(b)> = <Phi(a), b> for real a, b: p is real and even in k (so the padded circular
+    # convolution's kernel is symmetric) and the ball's node set is closed under k -> -k; the
+    # adjoint of the time-splitting step relies on it
+    rng = np.random.default_rng(5)
+    n, lo, ln, X, Y, Z = _grid(16, 5.0)
+    nax = np.array([0.3, -0.4, 0.866]) / np.linalg.norm([0.3, -0.4, 0.866])
+    m_axis = np.array([0.6, 0.0, 0.8])
+    a = rng.standard_normal(X.shape)
+    b = rng.standard_normal(X.shape)
+    pa = split.ddi_split(a, n, lo, ln, nax, m_axis, k0=1.0, nr=12, ntheta=8, nphi=16)
+    pb = split.ddi_split(b, n, lo, ln, nax, m_axis, k0=1.0, nr=12, ntheta=8, nphi=16)
+    lhs, rhs = float(np.sum(a * pb)), float(np.sum(pa * b))
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), np.sum(np.abs(a * pb)))

@@ -228,3 +228,19 @@ def test_split_full_size_sampled_points(D, full_split_ref, precision):
     ref = i1[idx[:, 2], idx[:, 1], idx[:, 0]] + nudft.type1_at(tb["W"] * rh, tb["k"], pts)
     got = phi[idx[:, 2], idx[:, 1], idx[:, 0]]
     assert _relinf(got, ref) <= TOL[precision]
+
+
+def test_describe_equals_the_built_plan(D):
+    # ddi_plan_describe (host only) reports what ddi_plan_create builds
+    w = synth.gaussian_mixture_density(32, 8.0, seed=1)
+    for kw in (dict(precision=1), dict(precision=0, split_k0=0.8), dict(precision=1, split_k0=0.8),
+               dict(precision=0, ellipsoid=True)):
+        desc = D.make_desc(3, w["n"], w["lo"], w["len"], w["axis"], **kw)
+        want = D.describe(desc)
+        plan = D.Plan(3, w["n"], w["lo"], w["len"], w["axis"], **kw)
+        got = plan.info
+        for f in ("dim", "precision", "width", "nodes", "nodes_used", "nr", "ntheta", "nphi", "ellipsoid"):
+            assert getattr(got, f) == getattr(want, f), f
+        assert list(got.nf) == list(want.nf) and list(got.band) == list(want.band)
+        assert got.kmax == want.kmax and got.split_k0 == want.split_k0
+        plan.close()

@@ -97,7 +97,15 @@ typedef struct {
                           passes only on the lines through its taps (|l_d| <= kmax h_d nf_d / (2 pi) +
                           w/2 + 2 around k = 0; the other lines are zero or never read); 1 => on
                           every line, as a plan without split_k0 does */
+  int spread;          /* type-1 spreading scheme: 0 => automatic (columns where they apply, else plane
+                          tiles); DDI_SPREAD_TILES => owner-computes tile planes in shared memory (`tile`,
+                          `chunk`); DDI_SPREAD_COLUMNS => 8 x 4-cell columns of the fine grid whose z-planes
+                          a warp accumulates in registers (FP32 3D plans whose fine grid is a multiple of
+                          8 in x and 4 in y and at least w + 7 cells in x, w + 3 in y and w in z;
+                          DDI_ERR_ARG otherwise; `chunk` = visits per work item) */
 } ddi_plan_desc;
+
+enum { DDI_SPREAD_AUTO = 0, DDI_SPREAD_TILES = 1, DDI_SPREAD_COLUMNS = 2 };
 
 /* Read-only facts about a built plan (sizes and the NUFFT parameters chosen). */
 typedef struct {
@@ -118,6 +126,8 @@ typedef struct {
   int ellipsoid;       /* 1 if the quadrature is the ellipsoidal rule */
   int band[2];         /* split plans: half-widths (x, y) of the band of fine-grid lines the ball's
                           y and z passes transform (0, 0: every line) */
+  int spread;          /* DDI_SPREAD_TILES or DDI_SPREAD_COLUMNS: the scheme the plan uses (0 from
+                          ddi_plan_describe) */
 } ddi_plan_info;
 
 /* Energies of Sec. 3.2 for a state phi (all FP64). */

@@ -63,6 +63,8 @@ std::vector<std::array<int, 3>> tile_candidates(const Plan& p) {
 }  // namespace
 
 int tune_spread_tile(Plan& p, cudaStream_t s) {
+  // the column spread has no tile (its columns are fixed); nothing to tune
+  if (p.spread_kind == DDI_SPREAD_COLUMNS) return DDI_OK;
   const std::string key = tune_key_of(p);
   std::unique_lock<std::mutex> lock(g_tune_mu);
   auto hit = g_tune_cache.find(key);
@@ -355,6 +357,7 @@ int build_batch(ddi_batch_s* b, ddi_batch* out, const ddi_plan_desc* descs, int 
   // host copies only needed while building
   for (Plan* p : b->plans) {
     std::vector<ushort4>().swap(p->h_l0);
+    std::vector<int>().swap(p->h_zcls);
     std::vector<int64_t>().swap(p->order);
     std::vector<double>().swap(p->quad.k);
     std::vector<double>().swap(p->quad.W);

@@ -95,6 +95,22 @@ struct SplitUnit {
   int tile, plane, slot0, nslots;
 };
 
+// ---- column spread work list (FP32 3D) -------------------------------------------------------
+// A column is a kColX x kColY block of fine cells in x-y with all its z-planes.  A work unit
+// takes a range of the column's visits, sorted by their first z tap, and a window of planes.
+constexpr int kColX = 8, kColY = 8;
+struct ColUnit {
+  int col;       // column index cy * (nf_x / kColX) + cx
+  int lo, hi;    // visit range
+  int z0, z1;    // planes [z0, z1) the unit writes (plane z mod nf_z; z1 may exceed nf_z)
+  int plo, phi;  // leading / trailing planes that other units also touch: go to partial slots
+  int slot0;     // its shared planes (leading, then trailing) are entries slot0 .. of the unit slot map
+};
+struct alignas(16) ColRed {  // a plane of a column touched by several units: the sum of their partial slots
+  int col, z;
+  int s0, ns;    // partial slots [s0, s0 + ns), one per unit touching the plane, in unit order
+};
+
 // ---- spread tile geometry (host and device) -------------------------------------------------
 constexpr int kSpreadThreads = 128;  // 4 warps per CTA, each taking work units on its own
 
@@ -145,6 +161,7 @@ struct Plan {
   QuadTables quad;                   // host copy of the tables (export, tests)
   std::vector<int64_t> order;        // processing order -> original node index
   std::vector<ushort4> h_l0;         // host copy of d_l0 (spread lists are rebuilt from it)
+  std::vector<int> h_zcls;           // z class of each processed node (equal first z tap and psi_z row)
   bool gpe_ready = false;            // GPE workspace allocated (plans of a batch have none)
   size_t spread_bytes = 0;           // device bytes of the spread lists and partial planes
   double tuned_ms = 0.0;             // spread time of the tile the autotuner chose (0: not tuned)
@@ -163,6 +180,16 @@ struct Plan {
   SpreadUnit* d_units = nullptr;
   SplitUnit* d_split = nullptr;
   int* d_counter = nullptr;   // unit counter of the persistent spread
+  // column spread (spread_kind == DDI_SPREAD_COLUMNS)
+  int spread_kind = DDI_SPREAD_TILES;
+  int2* d_cvis = nullptr;     // visits (node, first z tap << 13 | z-class start << 12 | (oy + 16) << 6 | (ox + 16))
+  ColUnit* d_cunits = nullptr;
+  ColRed* d_cred = nullptr;
+  int* d_cslots = nullptr;    // per unit (from its slot0): the partial slot of each shared plane
+  
+  void* d_cpart = nullptr;    // partial planes: [slot][kColY * kColX] complex
+  int ncunits = 0, ncred = 0, ncslots = 0;
+  int col_stage = 32;         // visits a warp stages at a time (16 or 32)
   long long visits = 0;       // total visit-list entries
   long long pairs = 0;        // total (node, plane) pairs of all units
   int npl = 1;                // owned planes per tile (z-planes in 3D; 1 in 2D)

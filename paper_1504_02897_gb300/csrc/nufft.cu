@@ -32,7 +32,9 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstddef>
 #include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -393,6 +395,311 @@ __global__ void __launch_bounds__(256)
   fine[((long long)gz * g.nf[1] + gy) * g.nf[0] + gx] = cmk<C>(sr, si);
 }
 
+// ---- column spreading (type 1, FP32 3D) -------------------------------------------------------
+// A warp owns one column of kColX x kColY = 8 x 8 fine cells in x-y (lane (lx, ly) holds the
+// cells (lx, ly) and (lx, ly + 4)) and W of its z-planes in registers: plane p (absolute,
+// unwrapped) lives in acc0/acc1[p mod W].  It streams the unit's visits in order of their
+// first z tap s: while zb < s the plane zb is complete (no later visit reaches it), so it
+// is written out and its registers cleared for plane zb + W.
+// Nodes with the same first z tap and the same psi_z row (a z class: one quadrature ring
+// has a single k_z) are consecutive in a column's list.  For such a run the lane first sums
+// g = sum c_q psi_x(x - l0x) psi_y(y - l0y) (one packed FP32 FMA per node and cell), then
+// adds g psi_z(p - s) to the W planes p = s .. s + W - 1 once: c psi_x psi_y psi_z summed in
+// the order (node, then z) instead of W products per node, exact up to rounding order.
+// psi_x psi_y is 0 outside the footprint.  No shared-memory read-modify-write and no
+// atomics: each cell belongs to one lane.
+// Nodes are staged NS at a time in the warp's shared memory: psi_z in rotated order, each
+// value twice (entry k holds plane k mod W of the node's window, so the add loop is the same
+// for every node and registers never move), psi_x and psi_y in zero-padded rows (a lane's
+// tap index needs no bounds test), and a header (first z tap with the run-start flag, byte
+// offsets of the node's psi_x / psi_y entries for the column's first cell, c_q).
+// Planes that several units touch go to partial slots (each such plane's slots are
+// contiguous, in unit order) that k_reduce_col sums in order (deterministic).  Planes
+// written directly use streaming stores, so they do not push the partial slots out of L2
+// before the reduction reads them.
+//
+// Row strides (words) are 4 mod 8, so the 16-byte stores of 8 consecutive lanes (each
+// writing its own node's row) fall in 8 distinct bank quadruples: conflict-free staging.
+static_assert(kColX == 8 && kColY == 8, "lane (lx, ly) holds cells (lx, ly) and (lx, ly + 4) of an 8 x 8 column");
+constexpr int kColThreads = 128;  // 4 warps per CTA, each taking units on its own
+template <int W, int NS>
+struct alignas(16) ColStage {
+  static constexpr int PZ = ((2 * W + 7) / 8) * 8 + 4;  // psi_z, rotated, each value twice, then padding
+  static constexpr int PX = ((W + 15 + 7) / 8) * 8 + 4;  // psi at [8, 8 + W): index c + 8 - o, c in [0, 8), o in [1-W, 8)
+  float pz[NS][PZ];
+  float px[NS][PX];
+  float py[NS][PX];
+  int4 hd[NS];  // byte offsets of px[j][8 - ox] and py[j][8 - oy]; c_q (two floats)
+  int sz[NS];   // first z tap
+};
+
+struct ColArgs {
+  int nf[3];
+  int ncx;
+  const ColUnit* units;
+  int nunits;
+  int* counter;
+  const int2* visits;
+  const float2* c;
+  const float* psi;  // [node][3][w]
+  float2* fine;
+  float2* partial;        // [slot][kColY * kColX]
+  const int* unit_slots;  // per unit: the partial slot of each leading, then trailing plane
+};
+
+// acc_k += g psi_z(k) for the run whose rotated, doubled psi_z row is pz
+template <int W>
+__device__ __forceinline__ void col_apply(float2 (&acc0)[W], float2 (&acc1)[W], const float* pz, float2 g0, float2 g1) {
+  const float4* p4 = reinterpret_cast<const float4*>(pz);
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k) {
+    const float4 v = p4[k];
+    const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
+    acc0[2 * k] = __ffma2_rn(g0, va, acc0[2 * k]);
+    acc1[2 * k] = __ffma2_rn(g1, va, acc1[2 * k]);
+    acc0[2 * k + 1] = __ffma2_rn(g0, vb, acc0[2 * k + 1]);
+    acc1[2 * k + 1] = __ffma2_rn(g1, vb, acc1[2 * k + 1]);
+  }
+  if constexpr (W % 2 == 1) {
+    const float2 v = reinterpret_cast<const float2*>(pz)[W - 1];
+    acc0[W - 1] = __ffma2_rn(g0, v, acc0[W - 1]);
+    acc1[W - 1] = __ffma2_rn(g1, v, acc1[W - 1]);
+  }
+}
+
+#define DDI_COL_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)
+
+template <int W, int NS>
+__global__ void __launch_bounds__(kColThreads) k_spread_col(ColArgs a) {
+  using S = ColStage<W, NS>;
+  static_assert(W <= 16, "planes 0..15 of the window");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  S* st = reinterpret_cast<S*>(smem_raw) + warp;
+  const int lx = lane & 7, ly = lane >> 3;
+  const int lx4 = 4 * lx, ly4 = 4 * ly;
+  const int nfx = a.nf[0], nfz = a.nf[2];
+  const long long plane = (long long)nfx * a.nf[1];
+  const unsigned st_off = (unsigned)(reinterpret_cast<unsigned char*>(st) - smem_raw);
+  // the zero padding of the psi_x / psi_y rows never changes: written once
+  for (int i = lane; i < NS * S::PX; i += 32) {
+    (&st->px[0][0])[i] = 0.f;
+    (&st->py[0][0])[i] = 0.f;
+  }
+  __syncwarp();
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(a.counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= a.nunits) break;
+    const ColUnit U = a.units[u];
+    const int cx = U.col % a.ncx, cy = U.col / a.ncx;
+    const long long cell = (long long)(cy * kColY + ly) * nfx + cx * kColX + lx;  // cell (lx, ly); + 4 nfx: (lx, ly + 4)
+    const int zpart_hi = U.z1 - U.phi;
+    float2 acc0[W], acc1[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
+    int zb = U.z0;
+    // write plane zb (direct, or a partial slot when other units touch it), clear its registers
+    auto flush = [&]() {
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+      switch (zb % W) {
+#define DDI_TAKE(R)                              \
+  case R:                                        \
+    if constexpr (R < W) {                       \
+      v0 = acc0[R];                              \
+      v1 = acc1[R];                              \
+      acc0[R] = acc1[R] = make_float2(0.f, 0.f); \
+    }                                            \
+    break;
+        DDI_COL_CASES(DDI_TAKE)
+#undef DDI_TAKE
+      }
+      const int r = zb - U.z0;
+      if (r < U.plo || zb >= zpart_hi) {
+        const int k = r < U.plo ? r : U.plo + (zb - zpart_hi);
+        float2* dst = a.partial + (size_t)__ldg(a.unit_slots + U.slot0 + k) * (kColX * kColY) + lane;
+        dst[0] = v0;
+        dst[32] = v1;
+      } else {
+        float2* dst = a.fine + (zb >= nfz ? zb - nfz : zb) * plane + cell;
+        __stcs(dst, v0);
+        __stcs(dst + 4 * nfx, v1);
+      }
+      ++zb;
+    };
+    for (int kb = U.lo; kb < U.hi; kb += NS) {
+      const int cnt = min(NS, U.hi - kb);
+      bool run_start = false;
+      if (lane < cnt) {
+        // one axis at a time, each stored as soon as it arrives (few registers live beside
+        // the accumulators)
+        const int2 v = a.visits[kb + lane];
+        run_start = (v.y >> 12) & 1;
+        const float* ps = a.psi + (size_t)v.x * 3 * W;
+        {
+          float t[W];
+          load_taps<float, W>(ps, t);
+#pragma unroll
+          for (int k = 0; k < W; ++k) st->px[lane][8 + k] = t[k];
+        }
+        {
+          float t[W];
+          load_taps<float, W>(ps + W, t);
+#pragma unroll
+          for (int k = 0; k < W; ++k) st->py[lane][8 + k] = t[k];
+        }
+        const int sz = v.y >> 13;
+        {
+          float t[W];
+          load_taps<float, W>(ps + 2 * W, t);
+          float2* pzr = reinterpret_cast<float2*>(st->pz[lane]);
+          const int rot = sz % W;  // tap dz feeds plane s + dz, held in register (s + dz) mod W
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            const int q = rot + k < W ? rot + k : rot + k - W;
+            pzr[q] = make_float2(t[k], t[k]);
+          }
+        }
+        const float2 cq = __ldg(a.c + v.x);
+        const int ox = (v.y & 63) - 16, oy = ((v.y >> 6) & 63) - 16;
+        const unsigned pxo = st_off + (unsigned)(offsetof(S, px) + (lane * S::PX + 8 - ox) * sizeof(float));
+        const unsigned pyo = st_off + (unsigned)(offsetof(S, py) + (lane * S::PX + 8 - oy) * sizeof(float));
+        st->hd[lane] = make_int4((int)pxo, (int)pyo, __float_as_int(cq.x), __float_as_int(cq.y));
+        st->sz[lane] = sz;
+      }
+      // runs of one z class: bit j set where staged visit j starts one (visit 0 always starts
+      // the batch's first run, which may continue a run of the previous batch)
+      unsigned starts = __ballot_sync(0xffffffffu, run_start) | 1u;
+      __syncwarp();
+      while (starts) {
+        const int j0 = __ffs(starts) - 1;
+        starts &= starts - 1;
+        const int j1 = starts ? __ffs(starts) - 1 : cnt;
+        const int sr = st->sz[j0];
+        while (zb < sr) flush();
+        // g: the run's sum of c psi_x psi_y per cell, then added to the W planes with psi_z
+        float2 g0 = make_float2(0.f, 0.f), g1 = g0;
+#pragma unroll 2
+        for (int j = j0; j < j1; ++j) {
+          const int4 h = st->hd[j];
+          const float wx = *reinterpret_cast<const float*>(smem_raw + h.x + lx4);
+          const float* py = reinterpret_cast<const float*>(smem_raw + h.y + ly4);
+          const float w0 = wx * py[0], w1 = wx * py[4];
+          const float2 cq = make_float2(__int_as_float(h.z), __int_as_float(h.w));
+          g0 = __ffma2_rn(make_float2(w0, w0), cq, g0);
+          g1 = __ffma2_rn(make_float2(w1, w1), cq, g1);
+        }
+        col_apply<W>(acc0, acc1, st->pz[j0], g0, g1);
+      }
+      __syncwarp();
+    }
+    while (zb < U.z1) flush();
+  }
+}
+
+// Planes of a column that several units touch: one warp per entry, a lane per two cells;
+// the entry's partial slots are contiguous (s0 .. s0 + ns - 1, in unit order) and summed in
+// that order (deterministic), eight loads in flight at a time.
+__global__ void __launch_bounds__(256)
+    k_reduce_col(const ColRed* __restrict__ red, int nred, const float2* __restrict__ partial,
+                 float2* __restrict__ fine, int nfx, int nfy, int ncx) {
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= nred) return;
+  const int lane = threadIdx.x & 31;
+  const int4 r = __ldg(reinterpret_cast<const int4*>(red) + e);  // col, z, s0, ns
+  const float4* src = reinterpret_cast<const float4*>(partial + (size_t)r.z * (kColX * kColY)) + lane;
+  // lane: cells 2 lane and 2 lane + 1 of the slot (row-major 8 x 8)
+  float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+  int k = 0;
+  for (; k + 8 <= r.w; k += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldcs(src + (size_t)(k + q) * (kColX * kColY / 2));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sum.x += v[q].x;
+      sum.y += v[q].y;
+      sum.z += v[q].z;
+      sum.w += v[q].w;
+    }
+  }
+  for (; k < r.w; ++k) {
+    const float4 v = __ldcs(src + (size_t)k * (kColX * kColY / 2));
+    sum.x += v.x;
+    sum.y += v.y;
+    sum.z += v.z;
+    sum.w += v.w;
+  }
+  const int cx = r.x % ncx, cy = r.x / ncx;
+  const int c0 = 2 * lane;  // row c0 / 8, columns c0 % 8 and c0 % 8 + 1
+  const long long cell = (long long)(cy * kColY + c0 / 8) * nfx + cx * kColX + c0 % 8;
+  *reinterpret_cast<float4*>(fine + (long long)r.y * nfx * nfy + cell) = sum;
+}
+
+template <int W, int NS>
+int configure_spread_col(Plan& p) {
+  const size_t smem = sizeof(ColStage<W, NS>) * (kColThreads / 32);
+  auto kern = k_spread_col<W, NS>;
+  {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    DDI_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      DDI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  int per_sm = 0;
+  DDI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kColThreads, smem));
+  int sms = 0;
+  DDI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device));
+  p.spread_smem = smem;
+  p.spread_blocks = std::max(1, std::min(per_sm * sms, (p.ncunits + kColThreads / 32 - 1) / (kColThreads / 32)));
+  return DDI_OK;
+}
+
+template <int W, int NS>
+int launch_spread_col(Plan& p, cudaStream_t s) {
+  ColArgs a;
+  for (int d = 0; d < 3; ++d) a.nf[d] = p.nf[d];
+  a.ncx = p.nf[0] / kColX;
+  a.units = p.d_cunits;
+  a.nunits = p.ncunits;
+  a.counter = p.d_counter;
+  a.visits = p.d_cvis;
+  a.c = static_cast<const float2*>(p.d_c);
+  a.psi = static_cast<const float*>(p.d_psi);
+  a.fine = static_cast<float2*>(p.d_fine);
+  a.partial = static_cast<float2*>(p.d_cpart);
+  a.unit_slots = p.d_cslots;
+  DDI_CUDA(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
+  k_spread_col<W, NS><<<p.spread_blocks, kColThreads, p.spread_smem, s>>>(a);
+  DDI_LAUNCH_CHECK();
+  p.mark("spread", s);
+  if (p.ncred > 0) {
+    k_reduce_col<<<(unsigned)((p.ncred + 7) / 8), 256, 0, s>>>(p.d_cred, p.ncred, static_cast<const float2*>(p.d_cpart),
+                                                               static_cast<float2*>(p.d_fine), p.nf[0], p.nf[1], a.ncx);
+    DDI_LAUNCH_CHECK();
+    p.mark("spread_reduce", s);
+  }
+  return DDI_OK;
+}
+
+template <int W>
+int spread_col_ns(Plan& p, cudaStream_t s, bool configure) {
+  if (p.col_stage == 16) return configure ? configure_spread_col<W, 16>(p) : launch_spread_col<W, 16>(p, s);
+  return configure ? configure_spread_col<W, 32>(p) : launch_spread_col<W, 32>(p, s);
+}
+
+int spread_col_w(Plan& p, cudaStream_t s, bool configure) {
+  switch (p.w) {
+    case 6: return spread_col_ns<6>(p, s, configure);
+    case 8: return spread_col_ns<8>(p, s, configure);
+  }
+  set_error("column spread: kernel width %d not built", p.w);
+  return DDI_ERR_ARG;
+}
+
 // ---- launch helpers ----------------------------------------------------------------------------
 template <typename T, int W, int DIM>
 int launch_interp(Plan& p, cudaStream_t s) {
@@ -495,6 +802,7 @@ DDI_WIDTH_SWITCH(configure_spread)
 }  // namespace
 
 int configure_kernels(Plan& p) {
+  if (p.spread_kind == DDI_SPREAD_COLUMNS) return spread_col_w(p, nullptr, /*configure=*/true);
   if (p.prec == DDI_FP64)
     return p.dim == 3 ? configure_spread_w<double, 3>(p, nullptr) : configure_spread_w<double, 2>(p, nullptr);
   return p.dim == 3 ? configure_spread_w<float, 3>(p, nullptr) : configure_spread_w<float, 2>(p, nullptr);
@@ -512,6 +820,7 @@ int time_spread(Plan& p, cudaStream_t s, int reps, float* ms) {
     return DDI_ERR_CUDA;
   }
   auto once = [&]() {
+    if (p.spread_kind == DDI_SPREAD_COLUMNS) return spread_col_w(p, s, false);
     if (p.prec == DDI_FP64) return p.dim == 3 ? launch_spread_w<double, 3>(p, s) : launch_spread_w<double, 2>(p, s);
     return p.dim == 3 ? launch_spread_w<float, 3>(p, s) : launch_spread_w<float, 2>(p, s);
   };
@@ -545,7 +854,11 @@ int run_type2(Plan& p, const T* rho, cudaStream_t s) {
 
 template <typename T>
 int run_type1(Plan& p, T* phi, cudaStream_t s, bool acc = false) {
-  DDI_TRY((p.dim == 3 ? launch_spread_w<T, 3>(p, s) : launch_spread_w<T, 2>(p, s)));
+  if (p.spread_kind == DDI_SPREAD_COLUMNS) {
+    DDI_TRY(spread_col_w(p, s, false));
+  } else {
+    DDI_TRY((p.dim == 3 ? launch_spread_w<T, 3>(p, s) : launch_spread_w<T, 2>(p, s)));
+  }
   return nufft_inverse_fft<T>(p, phi, s, acc);
 }
 

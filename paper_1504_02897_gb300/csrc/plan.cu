@@ -9,6 +9,8 @@
 // tile plane, long ones cut into pieces that write partial planes), and all
 // device workspace.  ddi_plan_create is the only call that allocates.
 #include <algorithm>
+#include <array>
+#include <climits>
 #include <cstdint>
 #include <cmath>
 #include <cstdarg>
@@ -95,7 +97,8 @@ void free_plan(Plan& p) {
   void* ptrs[] = {p.d_dirw,   p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_ones,  p.d_fine,
                   p.d_partial,
                   p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
-                  p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out};
+                  p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out, p.d_cvis, p.d_cunits, p.d_cred,
+                  p.d_cslots, p.d_cpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 8; ++i)
@@ -250,6 +253,172 @@ int build_spread(Plan& p, cudaStream_t stream) {
   return configure_kernels(p);
 }
 
+// Whether the column spread applies: FP32 3D plans whose fine grid holds whole columns and
+// is wide enough that a footprint meets a column (or a z-window) in one contiguous piece.
+bool columns_apply(const Plan& p) {
+  return p.dim == 3 && p.prec == DDI_FP32 && p.nf[0] % kColX == 0 && p.nf[1] % kColY == 0 &&
+         p.nf[0] >= kColX + p.w - 1 && p.nf[1] >= kColY + p.w - 1 && p.nf[2] >= p.w && p.w <= 16;
+}
+
+// Column spread lists.  Every processed node visits the columns its x-y taps reach; a
+// column's visits are sorted by the node's first z tap (then by node).  The visits are cut
+// into units of at most `chunk` visits; unit c writes the planes [a_c, e_c), a_c = its first
+// visit's first tap, e_c the end of its last footprint extended over the gap to the next
+// unit (at most 64 planes ahead; longer gaps and empty columns get units without visits that
+// only write zeros).  A plane that several units touch (their footprints overlap at unit
+// boundaries, and the last unit of a column wraps onto the first) is a leading or trailing
+// plane of each of them: those go to partial slots and a reduce entry sums them in unit order;
+// every other plane is written by its one unit.  Every fine cell is written once per apply.
+int build_spread_col(Plan& p, cudaStream_t stream) {
+  const int W = p.w, nfx = p.nf[0], nfy = p.nf[1], nfz = p.nf[2];
+  const int ncx = nfx / kColX, ncy = nfy / kColY, ncol = ncx * ncy;
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  for (void** q : {(void**)&p.d_cvis, (void**)&p.d_cunits, (void**)&p.d_cred, (void**)&p.d_cslots, &p.d_cpart})
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+  p.bytes -= p.spread_bytes;
+  const size_t before = p.bytes;
+  // visits: key (column, first z tap) and the packed entry
+  auto span = [&](int l, int nf, int B, int* first) {  // blocks of B cells a footprint from l reaches
+    *first = l / B;
+    const int last = ((l + W - 1) % nf) / B;
+    int k = last - *first;
+    if (k < 0) k += nf / B;
+    return k + 1;
+  };
+  std::vector<int> count(ncol + 1, 0);
+  for (int64_t i = 0; i < p.Mh; ++i) {
+    int fx, fy;
+    const int kx = span(p.h_l0[i].x, nfx, kColX, &fx), ky = span(p.h_l0[i].y, nfy, kColY, &fy);
+    for (int b = 0; b < ky; ++b)
+      for (int a = 0; a < kx; ++a) ++count[((fy + b) % ncy) * ncx + (fx + a) % ncx];
+  }
+  std::vector<int> start(ncol + 1, 0);
+  for (int c = 0; c < ncol; ++c) start[c + 1] = start[c] + count[c];
+  const long long total = start[ncol];
+  if (total > (long long)INT32_MAX - 1 || p.Mh > (int64_t)INT32_MAX) {
+    set_error("%lld column-spread visits exceed the 32-bit visit lists; use fewer quadrature nodes", total);
+    return DDI_ERR_ARG;
+  }
+  std::vector<int2> vis((size_t)total);
+  {
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < p.Mh; ++i) {
+      const ushort4 l = p.h_l0[i];
+      int fx, fy;
+      const int kx = span(l.x, nfx, kColX, &fx), ky = span(l.y, nfy, kColY, &fy);
+      for (int b = 0; b < ky; ++b)
+        for (int a = 0; a < kx; ++a) {
+          const int bx = (fx + a) % ncx, by = (fy + b) % ncy;
+          const int ox = rel_start(l.x, bx * kColX, nfx, W), oy = rel_start(l.y, by * kColY, nfy, W);
+          if (ox < -(W - 1) || ox >= kColX || oy < -(W - 1) || oy >= kColY) {
+            set_error("column spread: footprint offset (%d, %d) outside its column", ox, oy);
+            return DDI_ERR_INTERNAL;
+          }
+          vis[fill[by * ncx + bx]++] = make_int2((int)i, ((int)l.z << 13) | ((oy + 16) << 6) | (ox + 16));
+        }
+    }
+  }
+  // per column: by first z tap, then z class (nodes with the same first tap and bit-identical
+  // psi_z rows, e.g. one quadrature ring), then node (the visits are in node order already);
+  // bit 12 marks the first visit of each run of one z class
+  for (int c = 0; c < ncol; ++c) {
+    auto b = vis.begin() + start[c], e = vis.begin() + start[c + 1];
+    std::stable_sort(b, e, [&](const int2& u, const int2& v) {
+      const int su = u.y >> 13, sv = v.y >> 13;
+      return su != sv ? su < sv : p.h_zcls[u.x] < p.h_zcls[v.x];
+    });
+    for (auto it = b; it != e; ++it)
+      if (it == b || p.h_zcls[it->x] != p.h_zcls[(it - 1)->x]) it->y |= 1 << 12;
+  }
+  const int cap = p.desc.chunk > 0 ? p.desc.chunk : 256;
+  const int lmax = std::min(64, nfz);
+  std::vector<ColUnit> units;
+  std::vector<ColRed> red;
+  std::vector<int> slots;  // per unit-local shared plane: its partial slot
+  int nslot = 0, nslot_e = 0;
+  std::vector<int> tc(nfz);
+  std::vector<std::vector<int>> contrib(nfz);
+  for (int c = 0; c < ncol; ++c) {
+    const int b0 = start[c], b1 = start[c + 1];
+    const size_t u0 = units.size();
+    if (b0 == b1) {
+      for (int z = 0; z < nfz; z += lmax) units.push_back(ColUnit{c, b0, b0, z, std::min(nfz, z + lmax), 0, 0, 0});
+      continue;
+    }
+    // visit chunks and their planes [a, b) (b = last first tap + w)
+    std::vector<std::array<int, 4>> ch;  // lo, hi, a, b
+    for (int k = b0; k < b1; k += cap) {
+      const int hi = std::min(b1, k + cap);
+      ch.push_back({{k, hi, vis[k].y >> 13, (vis[hi - 1].y >> 13) + W}});
+    }
+    const int nch = (int)ch.size();
+    for (int k = 0; k < nch; ++k) {
+      const int a = ch[k][2];
+      const int next = k + 1 < nch ? ch[k + 1][2] : ch[0][2] + nfz;
+      const int e = std::max(ch[k][3], std::min(next, a + lmax));
+      units.push_back(ColUnit{c, ch[k][0], ch[k][1], a, e, 0, 0, 0});
+      for (int z = e; z < next; z += lmax) units.push_back(ColUnit{c, ch[k][1], ch[k][1], z, std::min(next, z + lmax), 0, 0, 0});
+    }
+    // planes touched by several units
+    std::fill(tc.begin(), tc.end(), 0);
+    for (size_t u = u0; u < units.size(); ++u)
+      for (int z = units[u].z0; z < units[u].z1; ++z) ++tc[z % nfz];
+    for (size_t u = u0; u < units.size(); ++u) {
+      ColUnit& U = units[u];
+      const int len = U.z1 - U.z0;
+      int lo = 0, hi = 0;
+      while (lo < len && tc[(U.z0 + lo) % nfz] > 1) ++lo;
+      if (lo < len)
+        while (hi < len - lo && tc[(U.z1 - 1 - hi) % nfz] > 1) ++hi;
+      for (int r = lo; r < len - hi; ++r)
+        if (tc[(U.z0 + r) % nfz] != 1) {
+          set_error("column spread: shared plane inside a unit's window");
+          return DDI_ERR_INTERNAL;
+        }
+      U.plo = lo;
+      U.phi = hi;
+      U.slot0 = nslot;
+      for (int r = 0; r < lo; ++r) contrib[(U.z0 + r) % nfz].push_back(nslot + r);
+      for (int r = 0; r < hi; ++r) contrib[(U.z1 - hi + r) % nfz].push_back(nslot + lo + r);
+      nslot += lo + hi;
+      slots.resize(nslot);
+    }
+    // slots entry-major: the contributions to one plane are contiguous, in unit order;
+    // slots[] maps each unit's k-th shared plane (unit-local numbering) to its slot
+    for (int z = 0; z < nfz; ++z) {
+      if (contrib[z].empty()) continue;
+      red.push_back(ColRed{c, z, nslot_e, (int)contrib[z].size()});
+      for (int q : contrib[z]) slots[q] = nslot_e++;
+      contrib[z].clear();
+    }
+  }
+  // costliest units first (visits, and the planes each writes)
+  std::stable_sort(units.begin(), units.end(), [](const ColUnit& a, const ColUnit& b) {
+    return (a.hi - a.lo) + (a.z1 - a.z0) > (b.hi - b.lo) + (b.z1 - b.z0);
+  });
+  if (units.size() > (size_t)INT32_MAX || slots.size() > (size_t)INT32_MAX) {
+    set_error("column spread: work list too long");
+    return DDI_ERR_ARG;
+  }
+  p.visits = total;
+  p.pairs = total;
+  p.chunk = cap;
+  p.ncunits = (int)units.size();
+  p.ncred = (int)red.size();
+  p.ncslots = nslot;
+  DDI_TRY(upload(p, (void**)&p.d_cvis, vis, "column visits", stream));
+  DDI_TRY(upload(p, (void**)&p.d_cunits, units, "column units", stream));
+  DDI_TRY(upload(p, (void**)&p.d_cred, red, "column reduce entries", stream));
+  DDI_TRY(upload(p, (void**)&p.d_cslots, slots, "column slot lists", stream));
+  DDI_TRY(dev_alloc(p, &p.d_cpart, p.cx_size() * kColX * kColY * (size_t)std::max(1, nslot), "column partial planes"));
+  p.spread_bytes = p.bytes - before;
+  DDI_CUDA(cudaStreamSynchronize(stream));
+  return configure_kernels(p);
+}
+
 int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool gpe) {
   std::string err;
   {
@@ -279,6 +448,13 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   p.M = p.quad.M;
   choose_tile(p);
   const int dim = d.dim, W = p.w;
+  if (d.spread == DDI_SPREAD_COLUMNS && !columns_apply(p)) {
+    set_error("the column spread needs an FP32 3D plan whose fine grid is a multiple of %d x %d in x-y and at "
+              "least w + %d, w + %d and w cells along x, y and z",
+              kColX, kColY, kColX - 1, kColY - 1);
+    return DDI_ERR_ARG;
+  }
+  p.spread_kind = (d.spread != DDI_SPREAD_TILES && columns_apply(p)) ? DDI_SPREAD_COLUMNS : DDI_SPREAD_TILES;
 
   // one node of each (k, -k) pair: the first half of the azimuth
   const int nphi = d.nphi, half = nphi / 2;
@@ -316,6 +492,24 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   l0s.assign(p.Mh, ushort4{});
   std::vector<double> psi((size_t)p.Mh * 3 * W, 1.0), scale(p.Mh);
   const double hw = 0.5 * (double)W;
+  // z classes: nodes whose first z tap and fractional z offset are equal have the same psi_z
+  // row (computed by the same operations), so the column spread can sum them before psi_z
+  p.h_zcls.assign(p.Mh, 0);
+  {
+    std::vector<std::pair<std::pair<int, uint64_t>, int64_t>> zk((size_t)p.Mh);
+    for (int64_t i = 0; i < p.Mh; ++i) {
+      uint64_t bits = 0;
+      const double f = dim == 3 ? fr[3 * perm[i] + 2] : 0.0;
+      std::memcpy(&bits, &f, sizeof bits);
+      zk[i] = std::make_pair(std::make_pair(dim == 3 ? l0w[3 * perm[i] + 2] : 0, bits), i);
+    }
+    std::sort(zk.begin(), zk.end());
+    int cls = -1;
+    for (size_t k = 0; k < zk.size(); ++k) {
+      if (k == 0 || zk[k].first != zk[k - 1].first) ++cls;
+      p.h_zcls[zk[k].second] = cls;
+    }
+  }
   for (int64_t i = 0; i < p.Mh; ++i) {
     const int64_t o = perm[i];
     p.order[i] = qs[o];
@@ -373,7 +567,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   // the host vectors above die with this frame: finish the uploads first
   DDI_CUDA(cudaStreamSynchronize(stream));
   std::vector<double>().swap(p.quad.dirw);
-  DDI_TRY(build_spread(p, stream));
+  DDI_TRY(p.spread_kind == DDI_SPREAD_COLUMNS ? build_spread_col(p, stream) : build_spread(p, stream));
   if (!gpe) return DDI_OK;
   const size_t N = (size_t)p.grid_points();
   DDI_TRY(dev_alloc(p, &p.d_psi1, cs * N, "gpe psi1"));
@@ -485,6 +679,14 @@ void fill_info(const Plan& p, ddi_plan_info* info) {
   info->ellipsoid = p.desc.ellipsoid;
   info->band[0] = p.band[0];
   info->band[1] = p.band[1];
+  info->spread = p.spread_kind;
+  if (p.spread_kind == DDI_SPREAD_COLUMNS) {
+    info->tile[0] = kColX;
+    info->tile[1] = kColY;
+    info->tile[2] = p.nf[2];
+    info->spread_items = p.ncunits;
+    info->spread_split_tiles = p.ncred;
+  }
 }
 
 void destroy_plan(Plan& p) { free_plan(p); }

@@ -135,6 +135,10 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
     if (d.ntheta == 0) d.ntheta = size_for(0.32 * K, 8);
     if (d.nphi == 0) d.nphi = size_for(0.64 * K, 16);
   }
+  if (d.spread != DDI_SPREAD_AUTO && d.spread != DDI_SPREAD_TILES && d.spread != DDI_SPREAD_COLUMNS) {
+    *err = "spread must be DDI_SPREAD_AUTO, DDI_SPREAD_TILES or DDI_SPREAD_COLUMNS";
+    return DDI_ERR_ARG;
+  }
   if (d.split_full_passes != 0 && d.split_full_passes != 1) {
     *err = "split_full_passes must be 0 or 1";
     return DDI_ERR_ARG;

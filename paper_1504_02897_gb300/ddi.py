@@ -36,7 +36,7 @@ class PlanDesc(ctypes.Structure):
                 ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
                 ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("split_k0", ctypes.c_double),
-                ("ellipsoid", ctypes.c_int), ("split_full_passes", ctypes.c_int)]
+                ("ellipsoid", ctypes.c_int), ("split_full_passes", ctypes.c_int), ("spread", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -47,7 +47,7 @@ class PlanInfo(ctypes.Structure):
                 ("interp_items", ctypes.c_int), ("kmax", ctypes.c_double), ("nr", ctypes.c_int),
                 ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("spread_tuned_ms", ctypes.c_double), ("split_k0", ctypes.c_double), ("ellipsoid", ctypes.c_int),
-                ("band", ctypes.c_int * 2)]
+                ("band", ctypes.c_int * 2), ("spread", ctypes.c_int)]
 
 
 class GpeNonlinearity(ctypes.Structure):
@@ -76,6 +76,7 @@ EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_pla
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
+SPREAD_AUTO, SPREAD_TILES, SPREAD_COLUMNS = 0, 1, 2
 
 _lib = None
 
@@ -139,14 +140,16 @@ def _check(status, where):
 
 def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
               precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0, ellipsoid=False,
-              split_full_passes=False):
+              split_full_passes=False, spread=0):
     """A plan descriptor (``ddi_plan_desc``).  split_k0 != 0 selects the improved split
     algorithm of Sec. 2.1 (Eq. 3.9), 3D only: window q = exp(-|k|^2/k0^2) with k0 = split_k0
     (< 0: the library's default), the quadrature on the small ball |k| <= kmax (0: 6 k0)
     and the smooth part by a zero-padded FFT convolution.  ellipsoid: the quadrature on the
     ellipsoid |k_d| <= pi / h_d (heterogeneous boxes, e.g. thin domains h_z = eps h_x).
     split_full_passes: a split plan's ball NUFFT transforms every fine-grid line instead of
-    the band around k = 0 that holds its taps (same result; for comparison)."""
+    the band around k = 0 that holds its taps (same result; for comparison).
+    spread: SPREAD_AUTO (columns where they apply), SPREAD_TILES or SPREAD_COLUMNS (the
+    type-1 spreading scheme, see ddi_plan_desc.spread)."""
     d = PlanDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -167,6 +170,7 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.split_k0 = float(split_k0)
     d.ellipsoid = 1 if ellipsoid else 0
     d.split_full_passes = 1 if split_full_passes else 0
+    d.spread = int(spread)
     return d
 
 

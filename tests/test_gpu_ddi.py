@@ -65,11 +65,14 @@ def test_ddi_anisotropic_gaussian_24(D, precision):
     assert _relinf(got, ref) <= TOL[precision]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_ddi_mixture_tilted_48(D, precision):
-    # several tiles and split (hot) tiles: 48^3, 8-Gaussian mixture, n = (sin 30, 0, cos 30)
+@pytest.mark.parametrize("precision,spread", [(0, 1), (1, 1), (1, 2)])
+def test_ddi_mixture_tilted_48(D, precision, spread):
+    # several tiles / columns and split (hot) tiles or shared column planes: 48^3,
+    # 8-Gaussian mixture, n = (sin 30, 0, cos 30); both spreading schemes in FP32
     w = synth.gaussian_mixture_density(48, 8.0, seed=1)
-    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=48, ntheta=24, nphi=48)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=48, ntheta=24, nphi=48,
+                 spread=spread)
+    assert plan.info.spread == spread
     assert plan.info.spread_split_tiles > 0
     got = _run(D, plan, w["rho"])
     ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(48, 24, 48))
@@ -81,11 +84,50 @@ def test_ddi_other_tile_shape_and_chunk(D, precision):
     # a different spread tiling (small chunks: many split tiles) gives the same sum
     w = synth.gaussian_mixture_density(48, 8.0, seed=4)
     plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, nr=48, ntheta=24, nphi=48,
-                 tile=(16, 16, 16), chunk=100)
+                 tile=(16, 16, 16), chunk=100, spread=1)
     assert plan.info.spread_split_tiles > 4
     got = _run(D, plan, w["rho"])
     ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(48, 24, 48))
     assert _relinf(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("chunk", [7, 64, 100000])
+def test_ddi_columns_chunk_sizes(D, chunk):
+    # column spread with tiny units (most planes shared by several units and summed by the
+    # reduce), default-like units, and one unit per column (its window wraps onto itself)
+    w = synth.gaussian_mixture_density(48, 8.0, seed=4)
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=1, nr=48, ntheta=24, nphi=48,
+                 chunk=chunk, spread=2)
+    assert plan.info.spread == 2 and tuple(plan.info.tile[:2]) == (8, 8)
+    got = _run(D, plan, w["rho"])
+    ref = _oracle(w["rho"], w["n"], w["lo"], w["len"], w["axis"], sizes=(48, 24, 48))
+    assert _relinf(got, ref) <= TOL[1]
+
+
+@pytest.mark.parametrize("n", [(8, 8, 8), (12, 8, 16)])
+def test_ddi_columns_small_fine_grids(D, n):
+    # the smallest fine grids (16 cells: a footprint covers most of a column and z-windows
+    # wrap), a ragged one, and the scheme the automatic choice makes for FP32 3D plans
+    rng = np.random.default_rng(8)
+    lo = tuple(-0.25 * v for v in n)
+    ln = tuple(0.5 * v for v in n)
+    X, Y, Z = synth.coords(n, lo, ln)
+    rho = np.exp(-(X ** 2 + Y ** 2 + Z ** 2)) * (1 + 0.05 * rng.random(X.shape))
+    plan = _plan(D, 3, n, lo, ln, (0, 0.6, 0.8), precision=1, nr=8, ntheta=6, nphi=8)
+    assert plan.info.spread == 2
+    got = _run(D, plan, rho)
+    ref = _oracle(rho, n, lo, ln, (0, 0.6, 0.8), sizes=(8, 6, 8))
+    assert _relinf(got, ref) <= TOL[1]
+
+
+def test_ddi_columns_rejected_where_they_do_not_apply(D):
+    # FP64 plans and 2D plans spread by tiles; asking for columns is an argument error
+    with pytest.raises(D.DDIError):
+        D.Plan(3, (16, 16, 16), (-1,) * 3, (2,) * 3, (0, 0, 1), precision=0, spread=2)
+    with pytest.raises(D.DDIError):
+        D.Plan(2, (16, 16), (-1,) * 2, (2,) * 2, (0, 0, 1), precision=1, spread=2)
+    p = D.Plan(3, (16, 16, 16), (-1,) * 3, (2,) * 3, (0, 0, 1), precision=0)
+    assert p.info.spread == 1
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -128,6 +128,8 @@ typedef struct {
                           y and z passes transform (0, 0: every line) */
   int spread;          /* DDI_SPREAD_TILES or DDI_SPREAD_COLUMNS: the scheme the plan uses (0 from
                           ddi_plan_describe) */
+  int yrange[2];       /* first fine-grid y line and number of lines (cyclic) that hold node taps; the
+                          NUFFT's z passes transform only their columns (0, 0 from ddi_plan_describe) */
 } ddi_plan_info;
 
 /* Energies of Sec. 3.2 for a state phi (all FP64). */

@@ -30,6 +30,7 @@ namespace {
 std::mutex g_tune_mu;
 struct TuneResult {
   std::array<int, 3> tile;
+  int chunk;  // column plans: visits per work unit
   double ms;
 };
 std::map<std::string, TuneResult> g_tune_cache;
@@ -62,9 +63,42 @@ std::vector<std::array<int, 3>> tile_candidates(const Plan& p) {
 
 }  // namespace
 
+// Column plans have fixed columns; the tuner picks the number of visits per work unit
+// (more units balance the load better, fewer share fewer planes through partial slots).
+int tune_column_chunk(Plan& p, cudaStream_t s) {
+  const std::string key = tune_key_of(p) + " columns";
+  std::unique_lock<std::mutex> lock(g_tune_mu);
+  auto hit = g_tune_cache.find(key);
+  if (hit != g_tune_cache.end()) {
+    const TuneResult r = hit->second;
+    lock.unlock();
+    p.desc.chunk = r.chunk;
+    DDI_TRY(build_spread_col(p, s));
+    p.tuned_ms = r.ms;
+    return DDI_OK;
+  }
+  int best = 0;
+  double best_ms = 0.0;
+  for (const int c : {128, 192, 256, 384, 512}) {
+    p.desc.chunk = c;
+    DDI_TRY(build_spread_col(p, s));
+    float ms = 0.f;
+    DDI_TRY(time_spread(p, s, 5, &ms));
+    if (best == 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  g_tune_cache[key] = TuneResult{{{0, 0, 0}}, best, best_ms};
+  lock.unlock();
+  p.desc.chunk = best;
+  DDI_TRY(build_spread_col(p, s));
+  p.tuned_ms = best_ms;
+  return DDI_OK;
+}
+
 int tune_spread_tile(Plan& p, cudaStream_t s) {
-  // the column spread has no tile (its columns are fixed); nothing to tune
-  if (p.spread_kind == DDI_SPREAD_COLUMNS) return DDI_OK;
+  if (p.spread_kind == DDI_SPREAD_COLUMNS) return tune_column_chunk(p, s);
   const std::string key = tune_key_of(p);
   std::unique_lock<std::mutex> lock(g_tune_mu);
   auto hit = g_tune_cache.find(key);
@@ -99,7 +133,7 @@ int tune_spread_tile(Plan& p, cudaStream_t s) {
     set_error("spread-tile autotuner: no candidate tile fits in shared memory");
     return DDI_ERR_ARG;
   }
-  g_tune_cache[key] = TuneResult{best, best_ms};
+  g_tune_cache[key] = TuneResult{best, 0, best_ms};
   lock.unlock();
   set_tile(p, best.data());
   DDI_TRY(build_spread(p, s));

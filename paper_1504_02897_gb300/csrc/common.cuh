@@ -200,6 +200,9 @@ struct Plan {
   // split plans: half-widths of the band of fine-grid lines around k = 0 that hold every tap
   // of the ball's nodes (x and y; 0 = all lines); the ball's NUFFT passes skip the others
   int band[2] = {0, 0};
+  // fine-grid y lines that hold node taps: yr[0], yr[0] + 1, .. (mod nf_y), yr[1] of them;
+  // the NUFFT's z passes transform only these columns and its y passes only store / read them
+  int yr[2] = {0, 1};
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n} (FP32: n heads, then n tails)
   // GPE workspace
@@ -286,6 +289,7 @@ int configure_kernels(Plan& p);  // per-plan launch geometry (nufft.cu)
 int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream, bool gpe = true);
 void set_tile(Plan& p, const int want[3]);         // tile rounded as for ddi_plan_desc.tile
 int build_spread(Plan& p, cudaStream_t stream);     // spread lists for the current tile
+int build_spread_col(Plan& p, cudaStream_t stream); // column spread lists for desc.chunk (plan.cu)
 int time_spread(Plan& p, cudaStream_t s, int reps, float* ms);  // best of reps (nufft.cu)
 int tune_spread_tile(Plan& p, cudaStream_t s);      // autotuner (batch.cu)
 void destroy_plan(Plan& p);

@@ -5,11 +5,16 @@
 //   forward  x: only the n^(d-1) rows through the padded block exist; their input is
 //               rho / psihat read straight from rho (pad and deconvolution fused);
 //            y: only the planes z in the block; elements outside the block read as zero;
-//            z: every column; elements outside the block read as zero.
-//   inverse  z: every column; only the z in the block are stored;
-//            y: only the planes z in the block; only the y in the block are stored;
+//               only the y lines that hold node taps are stored;
+//            z: the columns on those y lines; elements outside the block read as zero.
+//   inverse  z: the columns on those y lines; only the z in the block are stored;
+//            y: only the planes z in the block; elements on the other y lines read as
+//               zero (no tap reaches them); only the y in the block are stored;
 //            x: only the rows in the block; the x in the block are stored as
 //               Re(u) / psihat into phi (crop, deconvolution and real part fused).
+// The y lines with taps: one node of each (k, -k) pair is processed, the one with k_y >= 0
+// (the first half of the azimuth), so the taps lie on about half of the y lines (the plan
+// finds the shortest cyclic range holding all of them).
 // The NUFFT passes run once per evaluation and use the twiddles' FP32 heads only (the
 // path's error budget is 1e-6); the GPE's repeated transforms use heads and tails.
 // Split plans (Eq. 3.9) run the same six passes a second time for the smooth part I_1,
@@ -42,8 +47,19 @@ struct Geo {
   const T* dcy;
   const T* dcz;
   C* fine;
+  // the fine-grid y lines that hold node taps: ylo, ylo + 1, .. (mod nf_y), nyr of them
+  int ylo, nyr;
   __device__ long long fidx(int lz, int ly, int lx) const {
     return ((long long)lz * ay.nf + ly) * ax.nf + lx;
+  }
+  __host__ __device__ bool in_yr(int l) const {
+    int d = l - ylo;
+    if (d < 0) d += ay.nf;
+    return d < nyr;
+  }
+  __host__ __device__ int yr_line(int i) const {
+    const int l = ylo + i;
+    return l >= ay.nf ? l - ay.nf : l;
   }
 };
 
@@ -76,7 +92,8 @@ struct PadX {
   __device__ void store(const Ref& r, int i, C v) const { g.fine[r.fine + i] = v; }
 };
 
-// y lines of the planes z in the block: forward (pruned input) or inverse (pruned output)
+// y lines of the planes z in the block: forward (pruned input; only the y lines that hold
+// node taps are stored) or inverse (pruned output; the y lines without taps are zero)
 template <typename T, bool FWD>
 struct BlockY {
   using C = cx_t<T>;
@@ -89,25 +106,27 @@ struct BlockY {
     return g.fidx(g.az.fine_of((int)(L / g.ax.nf)), 0, (int)(L % g.ax.nf));
   }
   __device__ C load(Ref r, int i) const {
-    if (FWD && !g.ay.in_block(i)) return cmk<C>((T)0, (T)0);
+    if (FWD ? !g.ay.in_block(i) : !g.in_yr(i)) return cmk<C>((T)0, (T)0);
     return __ldg(g.fine + r + (long long)i * g.ax.nf);
   }
   __device__ void store(Ref r, int i, C v) const {
-    if (!FWD && !g.ay.in_block(i)) return;
+    if (FWD ? !g.in_yr(i) : !g.ay.in_block(i)) return;
     g.fine[r + (long long)i * g.ax.nf] = v;
   }
 };
 
-// z columns: forward (pruned input) or inverse (pruned output)
+// z columns whose y line holds node taps: forward (pruned input) or inverse (pruned output)
 template <typename T, bool FWD>
 struct AllZ {
   using C = cx_t<T>;
   static constexpr bool kPreciseTwiddles = false;
   using Ref = long long;  // the column's (y, x) offset
   Geo<T> g;
-  __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.ay.nf; }
+  __host__ __device__ long long nlines() const { return (long long)g.ax.nf * g.nyr; }
   __device__ bool contig() const { return false; }
-  __device__ Ref ref(long long L) const { return L; }
+  __device__ Ref ref(long long L) const {
+    return (long long)g.yr_line((int)(L / g.ax.nf)) * g.ax.nf + L % g.ax.nf;
+  }
   __device__ C load(Ref r, int i) const {
     if (FWD && !g.az.in_block(i)) return cmk<C>((T)0, (T)0);
     return __ldg(g.fine + (long long)i * g.ay.nf * g.ax.nf + r);
@@ -258,13 +277,15 @@ struct SmoothZ {
   }
 };
 
-// unit: the pad and crop without the deconvolution (the split algorithm's smooth part)
+// unit: the split algorithm's smooth part (a full convolution: every y line, no deconvolution)
 template <typename T>
 Geo<T> geo_of(Plan& p, bool unit = false) {
   Geo<T> g;
   g.ax = Axis{p.n[0], p.nf[0]};
   g.ay = Axis{p.n[1], p.nf[1]};
   g.az = Axis{p.n[2], p.nf[2]};
+  g.ylo = unit ? 0 : p.yr[0];
+  g.nyr = unit ? p.nf[1] : p.yr[1];
   const T* dc = static_cast<const T*>(unit ? p.d_ones : p.d_deconv);
   g.dcx = dc;
   g.dcy = dc + p.n[0];

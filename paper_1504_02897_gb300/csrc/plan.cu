@@ -345,7 +345,16 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
     const int b0 = start[c], b1 = start[c + 1];
     const size_t u0 = units.size();
     if (b0 == b1) {
-      for (int z = 0; z < nfz; z += lmax) units.push_back(ColUnit{c, b0, b0, z, std::min(nfz, z + lmax), 0, 0, 0});
+      // an empty column is written as zeros, unless none of its y lines holds a tap (the
+      // NUFFT's passes neither transform nor read those lines)
+      bool needed = false;
+      for (int r = 0; r < kColY; ++r) {
+        int d = (c / ncx) * kColY + r - p.yr[0];
+        if (d < 0) d += nfy;
+        needed = needed || d < p.yr[1];
+      }
+      if (needed)
+        for (int z = 0; z < nfz; z += lmax) units.push_back(ColUnit{c, b0, b0, z, std::min(nfz, z + lmax), 0, 0, 0});
       continue;
     }
     // visit chunks and their planes [a, b) (b = last first tap + w)
@@ -527,6 +536,32 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
     scale[i] = 2.0 * p.dv * p.quad.W[qs[o]];
   }
 
+  // the shortest cyclic range of fine y lines holding every tap (the complement of the
+  // longest run of lines no tap reaches); every line for split plans, whose smooth part
+  // shares the passes' geometry with full transforms
+  {
+    const int nfy = p.nf[1];
+    std::vector<char> hit(nfy, 0);
+    for (int64_t i = 0; i < p.Mh; ++i)
+      for (int t = 0; t < (dim >= 2 ? W : 1); ++t) hit[(l0s[i].y + t) % nfy] = 1;
+    int best = 0, best_end = 0;  // longest cyclic run of untouched lines, ending before best_end
+    int run = 0;
+    for (int k = 0; k < 2 * nfy; ++k) {
+      run = hit[k % nfy] ? 0 : std::min(run + 1, nfy);
+      if (run > best) {
+        best = run;
+        best_end = (k + 1) % nfy;
+      }
+    }
+    if (p.split() || best == 0 || p.Mh == 0) {
+      p.yr[0] = 0;
+      p.yr[1] = nfy;
+    } else {
+      p.yr[0] = best_end;  // the first touched line after the gap
+      p.yr[1] = nfy - best;
+    }
+  }
+
   // deconvolution factors 1/psihat(2 pi j'/nf), j' = j - n/2
   std::vector<double> dc;
   for (int a = 0; a < 3; ++a)
@@ -680,6 +715,8 @@ void fill_info(const Plan& p, ddi_plan_info* info) {
   info->band[0] = p.band[0];
   info->band[1] = p.band[1];
   info->spread = p.spread_kind;
+  info->yrange[0] = p.yr[0];
+  info->yrange[1] = p.yr[1];
   if (p.spread_kind == DDI_SPREAD_COLUMNS) {
     info->tile[0] = kColX;
     info->tile[1] = kColY;

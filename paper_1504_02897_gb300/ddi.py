@@ -47,7 +47,7 @@ class PlanInfo(ctypes.Structure):
                 ("interp_items", ctypes.c_int), ("kmax", ctypes.c_double), ("nr", ctypes.c_int),
                 ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("spread_tuned_ms", ctypes.c_double), ("split_k0", ctypes.c_double), ("ellipsoid", ctypes.c_int),
-                ("band", ctypes.c_int * 2), ("spread", ctypes.c_int)]
+                ("band", ctypes.c_int * 2), ("spread", ctypes.c_int), ("yrange", ctypes.c_int * 2)]
 
 
 class GpeNonlinearity(ctypes.Structure):

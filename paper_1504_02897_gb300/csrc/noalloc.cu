@@ -12,7 +12,9 @@
 // Set-up: host code cannot pass g_partials itself to a kernel (in host code the name is
 // only a host-side stand-in for the device symbol), so the first call on each device
 // looks up the array's device address with cudaGetSymbolAddress, with that device
-// current, and caches it.  That first call should come before any stream capture.
+// current, and caches it.  That first call should come before any stream capture.  A
+// cached address is checked on every call (cudaPointerGetAttributes, no allocation) and
+// looked up again if the device's context was reset since (cudaDeviceReset).
 //
 // All calls share the array and it keeps the last call's contents.  Every call writes
 // each partial it reads before reading it, so nothing needs clearing.  Calls whose work
@@ -65,63 +67,90 @@ __global__ void __launch_bounds__(kNoallocThreads)
   }
 }
 
-// sums the first `blocks` partials in index order (deterministic) into out[0..2]
-__global__ void k_sums_final(const double* part, int blocks, double* out) {
-  const int q = threadIdx.x;
-  if (q >= 3) return;
-  double s = 0.0;
-  for (int b = 0; b < blocks; ++b) s += part[(size_t)b * 4 + q];
-  out[q] = s;
+// sums the first `blocks` partials into out[0..2] in a fixed order (deterministic): thread t
+// adds the contiguous chunk t of the partials in index order, then the chunk sums are added
+// pairwise in a fixed tree
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) k_sums_final(const double* part, int blocks, double* out) {
+  __shared__ double sh[3][kFinalThreads];
+  const int t = threadIdx.x;
+  const int per = (blocks + kFinalThreads - 1) / kFinalThreads;
+  const int b0 = t * per, b1 = min(blocks, b0 + per);
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int b = b0; b < b1; ++b)
+    for (int q = 0; q < 3; ++q) v[q] += part[(size_t)b * 4 + q];
+  for (int q = 0; q < 3; ++q) sh[q][t] = v[q];
+  __syncthreads();
+  for (int o = kFinalThreads / 2; o > 0; o >>= 1) {
+    if (t < o)
+      for (int q = 0; q < 3; ++q) sh[q][t] += sh[q][t + o];
+    __syncthreads();
+  }
+  if (t < 3) out[t] = sh[t][0];
+}
+
+// device address of g_partials on the current device dev (looked up once, re-checked)
+int partials_address(int dev, double** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_addr[dev]) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, g_addr[dev]) == cudaSuccess && at.type == cudaMemoryTypeDevice &&
+        at.device == dev) {
+      *out = g_addr[dev];
+      return DDI_OK;
+    }
+    cudaGetLastError();
+    g_addr[dev] = nullptr;  // the context was reset: look the array up again
+  }
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_partials);
+  if (e != cudaSuccess) {
+    ddi::set_error("gpe_sums_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return DDI_ERR_CUDA;
+  }
+  g_addr[dev] = static_cast<double*>(ptr);
+  *out = g_addr[dev];
+  return DDI_OK;
 }
 
 }  // namespace
 
 extern "C" int gpe_sums_noalloc(const void* psi, const void* V, int64_t count, int precision, double* sums,
                                 void* stream) {
-  if (!psi || !V || !sums || count < 0 || (precision != DDI_FP64 && precision != DDI_FP32)) {
-    ddi::set_error("gpe_sums_noalloc: psi, V, sums must be non-NULL device pointers, count >= 0, "
-                   "precision DDI_FP64 or DDI_FP32");
-    return DDI_ERR_ARG;
-  }
-  if (count > kNoallocMax) {
-    ddi::set_error("gpe_sums_noalloc: count %lld exceeds the maximum %lld grid points of its fixed scratch",
-                   (long long)count, kNoallocMax);
-    return DDI_ERR_ARG;
-  }
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    ddi::set_error("gpe_sums_noalloc: no usable current device");
-    return DDI_ERR_CUDA;
-  }
-  double* part = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      void* ptr = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_partials);
-      if (e != cudaSuccess) {
-        ddi::set_error("gpe_sums_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-        return DDI_ERR_CUDA;
+  return ddi::guarded("gpe_sums_noalloc", [&]() -> int {
+    if (!psi || !V || !sums || count < 0 || (precision != DDI_FP64 && precision != DDI_FP32)) {
+      ddi::set_error("gpe_sums_noalloc: psi, V, sums must be non-NULL device pointers, count >= 0, "
+                     "precision DDI_FP64 or DDI_FP32");
+      return DDI_ERR_ARG;
+    }
+    if (count > kNoallocMax) {
+      ddi::set_error("gpe_sums_noalloc: count %lld exceeds the maximum %lld grid points of its fixed scratch",
+                     (long long)count, kNoallocMax);
+      return DDI_ERR_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+      cudaGetLastError();
+      ddi::set_error("gpe_sums_noalloc: no usable current device");
+      return DDI_ERR_CUDA;
+    }
+    double* part = nullptr;
+    DDI_TRY(partials_address(dev, &part));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long per = (long long)kNoallocThreads * kNoallocPerThread;
+    const int blocks = count == 0 ? 0 : (int)((count + per - 1) / per);
+    if (blocks > 0) {
+      if (precision == DDI_FP64) {
+        k_sums_partial<double><<<blocks, kNoallocThreads, 0, s>>>(static_cast<const double2*>(psi),
+                                                                  static_cast<const double*>(V), count, part);
+      } else {
+        k_sums_partial<float><<<blocks, kNoallocThreads, 0, s>>>(static_cast<const float2*>(psi),
+                                                                 static_cast<const float*>(V), count, part);
       }
-      g_addr[dev] = static_cast<double*>(ptr);
+      DDI_LAUNCH_CHECK();
     }
-    part = g_addr[dev];
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const long long per = (long long)kNoallocThreads * kNoallocPerThread;
-  const int blocks = count == 0 ? 0 : (int)((count + per - 1) / per);
-  if (blocks > 0) {
-    if (precision == DDI_FP64) {
-      k_sums_partial<double><<<blocks, kNoallocThreads, 0, s>>>(static_cast<const double2*>(psi),
-                                                                static_cast<const double*>(V), count, part);
-    } else {
-      k_sums_partial<float><<<blocks, kNoallocThreads, 0, s>>>(static_cast<const float2*>(psi),
-                                                               static_cast<const float*>(V), count, part);
-    }
+    k_sums_final<<<1, kFinalThreads, 0, s>>>(part, blocks, sums);
     DDI_LAUNCH_CHECK();
-  }
-  k_sums_final<<<1, 32, 0, s>>>(part, blocks, sums);
-  DDI_LAUNCH_CHECK();
-  return DDI_OK;
+    return DDI_OK;
+  });
 }

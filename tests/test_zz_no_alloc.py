@@ -36,6 +36,35 @@ def test_noalloc_sums_match_gpe_energy(precision, tol):
         assert abs(got[2] * dv - ref["Eint"]) <= tol * abs(ref["Eint"])
 
 
+def test_noalloc_calls_allocate_nothing():
+    # the property the entry point exists for: after a first call (which looks up the
+    # library's fixed scratch array), further calls leave the device's free memory as it
+    # is, also after other device allocations were made in between
+    import torch
+    from paper_1504_02897_gb300 import build, ddi
+    build.build()
+    ddi.load()
+    n, lo, ln = synth.box(64, 6.0)
+    psi = torch.from_numpy(synth.gpe_initial(n, lo, ln, (1, 1, 2), eps=0.1, seed=3)).cuda()
+    V = torch.from_numpy(synth.harmonic_trap(n, lo, ln, (1, 1, 2))).cuda()
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ddi.sums_noalloc(psi, V, sums)
+    torch.cuda.synchronize()
+    first = sums.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        ddi.sums_noalloc(psi, V, sums)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(sums, first)          # fixed-order reduction: bit-identical repeats
+    other = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")  # an allocation by someone else
+    ddi.sums_noalloc(psi, V, sums)
+    torch.cuda.synchronize()
+    assert torch.equal(sums, first)
+    del other
+
+
 def test_noalloc_rejects_oversized_count():
     import ctypes
     import torch

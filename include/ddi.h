@@ -103,6 +103,11 @@ typedef struct {
                           a warp accumulates in registers (FP32 3D plans whose fine grid is a multiple of
                           8 in x and 4 in y and at least w + 7 cells in x, w + 3 in y and w in z;
                           DDI_ERR_ARG otherwise; `chunk` = visits per work item) */
+  int check_finite;    /* NaN / Inf in rho: the pad pass of every evaluation records them in a device
+                          flag of the plan (at no cost for finite input).  0 => ddi_apply stays
+                          asynchronous and the flag is read by ddi_plan_check (and by ddi_apply_host,
+                          which synchronises anyway); 1 => ddi_apply also synchronises `stream` and
+                          returns DDI_ERR_NONFINITE when its input held a non-finite value */
 } ddi_plan_desc;
 
 enum { DDI_SPREAD_AUTO = 0, DDI_SPREAD_TILES = 1, DDI_SPREAD_COLUMNS = 2 };
@@ -177,12 +182,20 @@ int ddi_plan_describe(const ddi_plan_desc* desc, ddi_plan_info* info);
 /* Phi = U_dip * rho by the quadrature sum above, through the NUFFT: deconvolve and
  * pad rho into the 2x oversampled grid, FFT, interpolate at one node of each +-k pair,
  * multiply by 2 h^d W_q, spread, inverse FFT, crop, deconvolve, real part.
- * rho, phi: device pointers to n-sized real grids in the plan precision; may alias. */
+ * rho, phi: device pointers to n-sized real grids in the plan precision; may alias.
+ * Non-finite values in rho are recorded (see ddi_plan_desc.check_finite, ddi_plan_check);
+ * with check_finite = 1 the call synchronises and returns DDI_ERR_NONFINITE for them. */
 int ddi_apply(ddi_plan plan, const void* rho, void* phi, void* stream);
 
 /* Same, end to end from host memory: copies rho in, applies, copies phi out, and
- * synchronises `stream`.  rho_host / phi_host: host pointers (pinned recommended). */
+ * synchronises `stream`.  rho_host / phi_host: host pointers (pinned recommended).
+ * DDI_ERR_NONFINITE when rho held NaN or Inf (phi is then not meaningful). */
 int ddi_apply_host(ddi_plan plan, const void* rho_host, void* phi_host, void* stream);
+
+/* Synchronises `stream`, then reports whether any evaluation of the plan since the last
+ * check (or since creation) read a NaN or Inf in its rho: DDI_ERR_NONFINITE (and clears the
+ * record) or DDI_OK.  The input check of Sec. 3's iterations applied to the DDI's input. */
+int ddi_plan_check(ddi_plan plan, void* stream);
 
 /* ddi_apply with a CUDA event recorded on `stream` after every kernel launch; on
  * return (the stream is synchronised) names[i] / ms[i] hold the i-th launch's kernel
@@ -264,6 +277,28 @@ int gpe_ground_state(ddi_plan plan, void* phi, const void* V, double beta, doubl
  * (the step's contribution to dJ/dV_j).  One DDI of r (Phi is self-adjoint). */
 int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V,
                      const void* V, double beta, double lambda, double dt, void* stream);
+
+/* Gradient of a final-time observable with respect to the trap (the differentiable dynamics
+ * of Sec. 4.1, Eq. tssp2): J = h^d sum_j x_j^2 |psi_T,j|^2, x the coordinate along the grid's
+ * last axis (z in 3D, y in 2D; x_j = lo + j h), psi_T after nsteps gpe_step steps (each a
+ * full Strang step) from psi0 with trap V.
+ * gpe_trap_observable: the forward run alone.  psi0: device complex grid (read only);
+ *   psi_T: device complex grid receiving the final state (distinct from psi0); J: host
+ *   pointer.  Synchronises.
+ * gpe_trap_gradient: J and dJ/dV (grad_V: device real grid, overwritten) by the adjoint of
+ *   every step (gpe_step_adjoint), with checkpointed recomputation: the forward sweep keeps
+ *   the state every `checkpoint` steps, the backward sweep recomputes each segment's step
+ *   inputs from its checkpoint; the seed cotangent 2 x^2 psi_T and J are formed on the
+ *   device.  work: device buffer of the caller, at least gpe_trap_gradient_workspace bytes
+ *   (ceil(nsteps / checkpoint) + checkpoint + 2 complex grids).  Synchronises.
+ * DDI_ERR_ARG for NULL pointers, nsteps or checkpoint < 1, a short workspace;
+ * DDI_ERR_NONFINITE when J is not finite. */
+int gpe_trap_observable(ddi_plan plan, const void* psi0, const void* V, double beta, double lambda, double dt,
+                        int nsteps, void* psi_T, double* J, void* stream);
+int gpe_trap_gradient_workspace(ddi_plan plan, int nsteps, int checkpoint, size_t* bytes);
+int gpe_trap_gradient(ddi_plan plan, const void* psi0, const void* V, double beta, double lambda, double dt,
+                      int nsteps, int checkpoint, void* work, size_t work_bytes, double* J, void* grad_V,
+                      void* stream);
 
 /* ---- batches ---------------------------------------------------------------------- */
 /* Many DDI evaluations (Sec. 2.1, Eq. DDI-Trun1) in one call: item i has its own grid,

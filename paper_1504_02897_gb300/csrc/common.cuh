@@ -180,6 +180,7 @@ struct Plan {
   SpreadUnit* d_units = nullptr;
   SplitUnit* d_split = nullptr;
   int* d_counter = nullptr;   // unit counter of the persistent spread
+  int* d_nonfinite = nullptr; // set by the pad pass when rho holds NaN / Inf (cleared by checks)
   // column spread (spread_kind == DDI_SPREAD_COLUMNS)
   int spread_kind = DDI_SPREAD_TILES;
   int2* d_cvis = nullptr;     // visits (node, first z tap << 13 | z-class start << 12 | (oy + 16) << 6 | (ox + 16))
@@ -284,6 +285,9 @@ __host__ __device__ inline size_t spread_warp_bytes(size_t plane_bytes, size_t s
 }
 
 int configure_kernels(Plan& p);  // per-plan launch geometry (nufft.cu)
+// reads and clears the plan's non-finite-input record after synchronising s:
+// DDI_ERR_NONFINITE if it was set (plan.cu)
+int take_nonfinite(Plan& p, cudaStream_t s);
 
 // ---- plans (plan.cu) ------------------------------------------------------------------------
 int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream, bool gpe = true);

@@ -49,6 +49,7 @@ struct Geo {
   C* fine;
   // the fine-grid y lines that hold node taps: ylo, ylo + 1, .. (mod nf_y), nyr of them
   int ylo, nyr;
+  int* nonfinite;  // set when the pad pass reads a NaN / Inf
   __device__ long long fidx(int lz, int ly, int lx) const {
     return ((long long)lz * ay.nf + ly) * ax.nf + lx;
   }
@@ -87,7 +88,9 @@ struct PadX {
   __device__ C load(const Ref& r, int i) const {
     if (!g.ax.in_block(i)) return cmk<C>((T)0, (T)0);
     const int jx = g.ax.grid_of(i);
-    return cmk<C>(__ldg(rho + r.grid + jx) * (g.dcx[jx] * r.dy * r.dz), (T)0);
+    const T v = __ldg(rho + r.grid + jx);
+    if (!isfinite(v) && *(volatile int*)g.nonfinite == 0) atomicOr(g.nonfinite, 1);
+    return cmk<C>(v * (g.dcx[jx] * r.dy * r.dz), (T)0);
   }
   __device__ void store(const Ref& r, int i, C v) const { g.fine[r.fine + i] = v; }
 };
@@ -286,6 +289,7 @@ Geo<T> geo_of(Plan& p, bool unit = false) {
   g.az = Axis{p.n[2], p.nf[2]};
   g.ylo = unit ? 0 : p.yr[0];
   g.nyr = unit ? p.nf[1] : p.yr[1];
+  g.nonfinite = p.d_nonfinite;
   const T* dc = static_cast<const T*>(unit ? p.d_ones : p.d_deconv);
   g.dcx = dc;
   g.dcy = dc + p.n[0];

@@ -98,7 +98,7 @@ void free_plan(Plan& p) {
                   p.d_partial,
                   p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
                   p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out, p.d_cvis, p.d_cunits, p.d_cred,
-                  p.d_cslots, p.d_cpart};
+                  p.d_cslots, p.d_cpart, p.d_nonfinite};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 8; ++i)
@@ -593,6 +593,8 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
     DDI_TRY(upload_real(p, &p.d_ones, ones, "unit factors", stream, &k4));
   }
   DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
+  DDI_TRY(dev_alloc(p, (void**)&p.d_nonfinite, sizeof(int), "non-finite record"));
+  DDI_CUDA(cudaMemsetAsync(p.d_nonfinite, 0, sizeof(int), stream));
   DDI_TRY(dev_alloc(p, &p.d_c, cs * p.Mh, "node values"));
   DDI_TRY(dev_alloc(p, &p.d_fine, cs * p.fine_points(), "fine grid"));
   for (int a = 0; a < 3; ++a) {
@@ -727,6 +729,16 @@ void fill_info(const Plan& p, ddi_plan_info* info) {
 }
 
 void destroy_plan(Plan& p) { free_plan(p); }
+
+int take_nonfinite(Plan& p, cudaStream_t s) {
+  int flag = 0;
+  DDI_CUDA(cudaMemcpyAsync(&flag, p.d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DDI_CUDA(cudaStreamSynchronize(s));
+  if (!flag) return DDI_OK;
+  DDI_CUDA(cudaMemsetAsync(p.d_nonfinite, 0, sizeof(int), s));
+  set_error("the density held NaN or Inf");
+  return DDI_ERR_NONFINITE;
+}
 
 }  // namespace ddi
 
@@ -900,8 +912,22 @@ int ddi_apply(ddi_plan plan, const void* rho, void* phi, void* stream) {
     DDI_TRY(check_plan_ptrs(plan, rho, phi));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Plan& p = plan->p;
-    if (p.prec == DDI_FP64) return ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s);
-    return ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s);
+    if (p.prec == DDI_FP64) {
+      DDI_TRY(ddi::run_ddi<double>(p, static_cast<const double*>(rho), static_cast<double*>(phi), s));
+    } else {
+      DDI_TRY(ddi::run_ddi<float>(p, static_cast<const float*>(rho), static_cast<float*>(phi), s));
+    }
+    return p.desc.check_finite ? ddi::take_nonfinite(p, s) : DDI_OK;
+  });
+}
+
+int ddi_plan_check(ddi_plan plan, void* stream) {
+  return ddi::guarded("ddi_plan_check", [&]() -> int {
+    if (!plan) {
+      ddi::set_error("plan must not be NULL");
+      return DDI_ERR_ARG;
+    }
+    return ddi::take_nonfinite(plan->p, static_cast<cudaStream_t>(stream));
   });
 }
 
@@ -918,8 +944,7 @@ int ddi_apply_host(ddi_plan plan, const void* rho_host, void* phi_host, void* st
       DDI_TRY(ddi::run_ddi<float>(p, static_cast<const float*>(p.d_io_in), static_cast<float*>(p.d_io_out), s));
     }
     DDI_CUDA(cudaMemcpyAsync(phi_host, p.d_io_out, bytes, cudaMemcpyDeviceToHost, s));
-    DDI_CUDA(cudaStreamSynchronize(s));
-    return DDI_OK;
+    return ddi::take_nonfinite(p, s);  // synchronises s
   });
 }
 

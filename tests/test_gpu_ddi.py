@@ -199,6 +199,44 @@ def test_ddi_in_place_and_host_path(D):
     assert np.max(np.abs(rho.cpu().numpy() - ref)) <= 1e-6 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nonfinite_density_is_reported(D, precision):
+    # NaN / Inf in rho: ddi_apply with check_finite returns DDI_ERR_NONFINITE, the host
+    # path reports it, an asynchronous apply leaves it for ddi_plan_check, and a finite
+    # density afterwards passes (the record is cleared by each report)
+    import torch
+    w = synth.gaussian_mixture_density(32, 6.0, seed=3)
+    rho = w["rho"].copy()
+    bad = rho.copy()
+    bad[5, 7, 11] = np.nan
+    inf = rho.copy()
+    inf[20, 1, 30] = -np.inf
+    plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, check_finite=True)
+    dt = plan.real_dtype
+    for arr in (bad, inf):
+        with pytest.raises(D.DDIError) as e:
+            plan.apply(torch.from_numpy(arr).to("cuda", dt))
+        assert e.value.status == -4
+    good = plan.apply(torch.from_numpy(rho).to("cuda", dt))
+    assert bool(torch.isfinite(good).all())
+    # asynchronous plan: recorded, reported by the check, then cleared
+    plan2 = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision)
+    plan2.apply(torch.from_numpy(bad).to("cuda", dt))
+    with pytest.raises(D.DDIError) as e:
+        plan2.check()
+    assert e.value.status == -4
+    plan2.check()
+    plan2.apply(torch.from_numpy(rho).to("cuda", dt))
+    plan2.check()
+    # host path
+    host_in = torch.from_numpy(bad.astype(np.float64 if precision == 0 else np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    with pytest.raises(D.DDIError) as e:
+        plan2.apply_host(host_in, host_out)
+    assert e.value.status == -4
+    plan2.check()
+
+
 def test_nonunit_axis_rejected(D):
     with pytest.raises(D.DDIError):
         D.Plan(3, (16, 16, 16), (-1,) * 3, (2,) * 3, (0, 0, 2))

@@ -115,6 +115,7 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert L.ddi_batch_apply(None, None, None, None) == -1
     assert L.ddi_batch_get_info(None, 0, None) == -1
     assert L.ddi_batch_graph_stats(None, None, None) == -1
+    assert L.ddi_plan_check(None, None) == -1
     out = ctypes.c_void_p()
     desc = lib.make_desc(3, (16, 16, 16), (-1, -1, -1), (2, 2, 2), (0, 0, 1))
     assert L.ddi_batch_create(None, ctypes.byref(desc), 1, 0, None) == -1
@@ -320,3 +321,24 @@ def test_split_band_holds_every_ball_tap(lib, precision):
     # a band that would cover the axis is not used
     coarse = lib.make_desc(3, (32,) * 3, (-8,) * 3, (16,) * 3, (0, 0, 1), precision=0, split_k0=0.8)
     assert list(lib.describe(coarse).band) == [0, 0]
+
+
+def test_noalloc_binding_rejects_mismatched_dtypes(lib):
+    # the binding checks dtypes before anything reaches the library (a complex128 psi with a
+    # float32 V would make the kernel read past V's end)
+    import torch
+    sums = torch.zeros(3, dtype=torch.float64)
+    for psi, V in ((torch.zeros(8, dtype=torch.complex128), torch.zeros(8, dtype=torch.float32)),
+                   (torch.zeros(8, dtype=torch.complex64), torch.zeros(8, dtype=torch.float64)),
+                   (torch.zeros(8, dtype=torch.float32), torch.zeros(8, dtype=torch.float32))):
+        with pytest.raises(ValueError):
+            lib.sums_noalloc(psi, V, sums)
+
+
+@pytest.mark.parametrize("field,value", [("spread", 3), ("spread", -1), ("check_finite", 2)])
+def test_scheme_fields_validated(lib, field, value):
+    desc = lib.make_desc(3, (16, 16, 16), (-1, -1, -1), (2, 2, 2), (0, 0, 1))
+    setattr(desc, field, value)
+    with pytest.raises(lib.DDIError) as e:
+        lib.quadrature_tables(desc)
+    assert e.value.status == -1

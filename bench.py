@@ -267,6 +267,27 @@ def kernel_bytes(name, info, real=4):
     return table.get(smooth.get(name, name), 0)
 
 
+def profile_driver(args):
+    """The 128^3 workload's DDI (8-Gaussian mixture, seed 0, on [-12,12)^3, axis (sin 30, 0,
+    cos 30), quadrature 128 x 64 x 128, autotuned spread; --split: the split algorithm with the
+    library's default window and ball) evaluated args.repeat times, for profilers."""
+    import torch
+    from paper_1504_02897_gb300 import build, ddi, synth
+    build.build()
+    ddi.load()
+    w = synth.gaussian_mixture_density(N, L, seed=0)
+    prec = ddi.FP32 if args.precision == "fp32" else ddi.FP64
+    sizes = dict(split_k0=-1.0) if args.split else dict(SIZES)
+    plan = ddi.Plan(3, w["n"], w["lo"], w["len"], w["axis"], precision=prec, tile=(-1, 0, 0), **sizes)
+    rho = torch.from_numpy(w["rho"]).to("cuda", plan.real_dtype)
+    out = torch.empty_like(rho)
+    for _ in range(args.repeat):
+        plan.apply(rho, out)
+    torch.cuda.synchronize()
+    print("ok", float(out.abs().max()), "spread", "columns" if plan.info.spread == 2 else "tiles",
+          list(plan.info.tile))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,8 +303,18 @@ def main():
                          "improved split algorithm (Eq. 3.9); batch2d_96: 96 2D densities in one batch; "
                          "tsfp128 / gs128 / grad128: the GPE step, ground state and trap gradient at 128^3")
     ap.add_argument("--fp64-check", type=int, default=1, help="grad128: also run the FP64 path for its error")
+    ap.add_argument("--profile-driver", action="store_true",
+                    help="no timing and no JSON: build the 128^3 workload's plan and call ddi_apply --repeat "
+                         "times (the command profilers capture)")
+    ap.add_argument("--repeat", type=int, default=2, help="--profile-driver: evaluations")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="--profile-driver: plan precision")
+    ap.add_argument("--split", action="store_true",
+                    help="--profile-driver: the split algorithm's workload (library defaults for window and ball)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_driver:
+        profile_driver(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

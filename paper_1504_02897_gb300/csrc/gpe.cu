@@ -7,6 +7,7 @@
 // unnormalised, so every Fourier-space multiplier below carries the 1/N_tot factor.
 // Reductions accumulate in FP64 per thread, per block (fixed order), then one block
 // sums the block partials in a fixed order: results are deterministic.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -437,6 +438,27 @@ unsigned blocks_for(long long total) {
 }
 
 // ---- host helpers ------------------------------------------------------------------------------
+// The observable of the trap-gradient problem, J = h^d sum_j x_j^2 |psi_j|^2 with x the
+// coordinate along the grid's last axis (z in 3D, y in 2D), and its cotangent for the real
+// pairing Re h^d sum conj(a) b: dJ/dpsi = 2 x^2 psi (written to cot when it is not null).
+template <typename T>
+__global__ void k_observable(const cx_t<T>* __restrict__ psi, cx_t<T>* __restrict__ cot, G3 g, int last, double lo,
+                             double h, double* part) {
+  double v[1] = {0.0};
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    idx3(i, g, x, y, z);
+    const int j = last == 2 ? z : (last == 1 ? y : x);
+    const double c = lo + (double)j * h;
+    const cx_t<T> a = psi[i];
+    v[0] += c * c * ((double)a.x * a.x + (double)a.y * a.y);
+    if (cot) cot[i] = cmk<cx_t<T>>((T)(2.0 * c * c) * a.x, (T)(2.0 * c * c) * a.y);
+  }
+  block_sum<1>(v, part + (size_t)blockIdx.x * kRedMax);
+}
+
 template <typename T>
 struct Gpe {
   using C = cx_t<T>;
@@ -572,6 +594,64 @@ struct Gpe {
       k_nonlinear_general<T><<<blocks_for(N), kThreads, 0, s>>>(psi, V, phi, (T)beta, (T)lam, (T)dt, nl, N);
       DDI_LAUNCH_CHECK();
       DDI_TRY(kinetic(psi, k + 1 < nsteps ? -0.5 * dt : -0.25 * dt));
+    }
+    return DDI_OK;
+  }
+
+  // J of the state psi (FP64 reduction; synchronises) and, when cot is not null, its cotangent
+  int observable(const C* psi, C* cot, double* J) {
+    const int last = p.dim - 1;
+    k_observable<T><<<p.red_blocks, kThreads, 0, s>>>(psi, cot, g, last, p.desc.lo[last], p.h[last], p.d_red);
+    DDI_LAUNCH_CHECK();
+    double sum = 0.0;
+    DDI_TRY(reduce(1, 0, &sum));
+    *J = p.dv * sum;
+    if (!std::isfinite(*J)) {
+      set_error("the observable is not finite");
+      return DDI_ERR_NONFINITE;
+    }
+    return DDI_OK;
+  }
+
+  // states kept by trap_gradient: checkpoints every `every` steps, then one segment's step inputs
+  static size_t trap_states(int nsteps, int every) { return (size_t)((nsteps + every - 1) / every) + (size_t)every; }
+
+  // nsteps single Strang steps from psi0 into cur (cur != psi0), then J; the forward run alone
+  int trap_forward(const C* psi0, C* cur, const T* V, double beta, double lam, double dt, int nsteps, double* J) {
+    DDI_CUDA(cudaMemcpyAsync(cur, psi0, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < nsteps; ++k) DDI_TRY(step(cur, V, beta, lam, dt, 1));
+    return observable(cur, nullptr, J);
+  }
+
+  // J after nsteps steps and dJ/dV by the hand-written adjoint of each step, with
+  // checkpointed recomputation: the forward sweep keeps the state every `every` steps, the
+  // backward sweep recomputes each segment's step inputs from its checkpoint and applies the
+  // step adjoints in reverse.  work: trap_states(nsteps, every) + 2 states.
+  int trap_gradient(const C* psi0, const T* V, double beta, double lam, double dt, int nsteps, int every, C* work,
+                    double* J, T* grad) {
+    const int ncp = (nsteps + every - 1) / every;
+    C* ckpt = work;                               // [ncp]
+    C* seg = work + (size_t)ncp * N;              // [every]: one segment's step inputs
+    C* cur = seg + (size_t)every * N;             // the running state
+    C* cot = cur + N;                             // the cotangent
+    DDI_CUDA(cudaMemcpyAsync(cur, psi0, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < nsteps; ++k) {
+      if (k % every == 0) DDI_CUDA(cudaMemcpyAsync(ckpt + (size_t)(k / every) * N, cur, sizeof(C) * N,
+                                                   cudaMemcpyDeviceToDevice, s));
+      DDI_TRY(step(cur, V, beta, lam, dt, 1));
+    }
+    DDI_TRY(observable(cur, cot, J));
+    DDI_CUDA(cudaMemsetAsync(grad, 0, sizeof(T) * N, s));
+    for (int c = ncp - 1; c >= 0; --c) {
+      const int k0 = c * every, k1 = std::min(nsteps, k0 + every);
+      DDI_CUDA(cudaMemcpyAsync(seg, ckpt + (size_t)c * N, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+      for (int k = k0 + 1; k < k1; ++k) {
+        C* prev = seg + (size_t)(k - 1 - k0) * N;
+        C* next = prev + N;
+        DDI_CUDA(cudaMemcpyAsync(next, prev, sizeof(C) * N, cudaMemcpyDeviceToDevice, s));
+        DDI_TRY(step(next, V, beta, lam, dt, 1));
+      }
+      for (int k = k1 - 1; k >= k0; --k) DDI_TRY(adjoint(seg + (size_t)(k - k0) * N, cot, grad, V, beta, lam, dt));
     }
     return DDI_OK;
   }
@@ -817,6 +897,68 @@ int gpe_step_adjoint(ddi_plan plan, const void* psi_in, void* cot, void* grad_V,
     Gpe<float> g(plan->p, s);
     return g.adjoint(static_cast<const float2*>(psi_in), static_cast<float2*>(cot), static_cast<float*>(grad_V),
                      static_cast<const float*>(V), beta, lambda, dt);
+  });
+}
+
+int gpe_trap_observable(ddi_plan plan, const void* psi0, const void* V, double beta, double lambda, double dt,
+                        int nsteps, void* psi_T, double* J, void* stream) {
+  return ddi::guarded("gpe_trap_observable", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, psi0, V));
+    DDI_TRY(ddi::check_gpe(plan, psi_T, V));
+    if (!J || nsteps < 0 || psi_T == psi0 || !ddi::finite_params({beta, lambda, dt})) {
+      ddi::set_error("gpe_trap_observable: J must not be NULL, psi_T must differ from psi0, nsteps >= 0, "
+                     "beta, lambda, dt finite");
+      return DDI_ERR_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.trap_forward(static_cast<const double2*>(psi0), static_cast<double2*>(psi_T),
+                            static_cast<const double*>(V), beta, lambda, dt, nsteps, J);
+    }
+    Gpe<float> g(plan->p, s);
+    return g.trap_forward(static_cast<const float2*>(psi0), static_cast<float2*>(psi_T), static_cast<const float*>(V),
+                          beta, lambda, dt, nsteps, J);
+  });
+}
+
+int gpe_trap_gradient_workspace(ddi_plan plan, int nsteps, int checkpoint, size_t* bytes) {
+  return ddi::guarded("gpe_trap_gradient_workspace", [&]() -> int {
+    if (!plan || !bytes || nsteps < 1 || checkpoint < 1) {
+      ddi::set_error("gpe_trap_gradient_workspace: plan and bytes must not be NULL, nsteps and checkpoint >= 1");
+      return DDI_ERR_ARG;
+    }
+    const size_t states = Gpe<double>::trap_states(nsteps, checkpoint) + 2;
+    *bytes = states * (size_t)plan->p.grid_points() * plan->p.cx_size();
+    return DDI_OK;
+  });
+}
+
+int gpe_trap_gradient(ddi_plan plan, const void* psi0, const void* V, double beta, double lambda, double dt,
+                      int nsteps, int checkpoint, void* work, size_t work_bytes, double* J, void* grad_V,
+                      void* stream) {
+  return ddi::guarded("gpe_trap_gradient", [&]() -> int {
+    DDI_TRY(ddi::check_gpe(plan, psi0, V));
+    DDI_TRY(ddi::check_gpe(plan, work, grad_V));
+    size_t need = 0;
+    if (!J || nsteps < 1 || checkpoint < 1 || !ddi::finite_params({beta, lambda, dt})) {
+      ddi::set_error("gpe_trap_gradient: J must not be NULL, nsteps and checkpoint >= 1, beta, lambda, dt finite");
+      return DDI_ERR_ARG;
+    }
+    DDI_TRY(gpe_trap_gradient_workspace(plan, nsteps, checkpoint, &need));
+    if (work_bytes < need) {
+      ddi::set_error("gpe_trap_gradient: workspace of %zu bytes, %zu needed", work_bytes, need);
+      return DDI_ERR_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan->p.prec == DDI_FP64) {
+      Gpe<double> g(plan->p, s);
+      return g.trap_gradient(static_cast<const double2*>(psi0), static_cast<const double*>(V), beta, lambda, dt,
+                             nsteps, checkpoint, static_cast<double2*>(work), J, static_cast<double*>(grad_V));
+    }
+    Gpe<float> g(plan->p, s);
+    return g.trap_gradient(static_cast<const float2*>(psi0), static_cast<const float*>(V), beta, lambda, dt, nsteps,
+                           checkpoint, static_cast<float2*>(work), J, static_cast<float*>(grad_V));
   });
 }
 

@@ -36,7 +36,8 @@ class PlanDesc(ctypes.Structure):
                 ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
                 ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("split_k0", ctypes.c_double),
-                ("ellipsoid", ctypes.c_int), ("split_full_passes", ctypes.c_int), ("spread", ctypes.c_int)]
+                ("ellipsoid", ctypes.c_int), ("split_full_passes", ctypes.c_int), ("spread", ctypes.c_int),
+                ("check_finite", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -72,7 +73,8 @@ EXPORTS = ["ddi_status_str", "ddi_last_error", "ddi_quadrature_tables", "ddi_pla
            "ddi_plan_get_info", "ddi_apply", "ddi_apply_host", "ddi_apply_timed", "ddi_type2", "ddi_type1", "ddi_plan_node_order",
            "gpe_step", "gpe_energy", "gpe_ground_state", "gpe_step_adjoint", "gpe_sums_noalloc",
            "ddi_batch_create", "ddi_batch_destroy", "ddi_batch_size", "ddi_batch_get_info", "ddi_batch_apply",
-           "ddi_batch_graph_stats", "ddi_plan_set_axes", "gpe_step_ex", "ddi_plan_describe"]
+           "ddi_batch_graph_stats", "ddi_plan_set_axes", "gpe_step_ex", "ddi_plan_describe", "ddi_plan_check",
+           "gpe_trap_observable", "gpe_trap_gradient_workspace", "gpe_trap_gradient"]
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
@@ -104,6 +106,7 @@ def load():
         "ddi_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], ci),
         "ddi_plan_describe": ([ctypes.POINTER(PlanDesc), ctypes.POINTER(PlanInfo)], ci),
         "ddi_apply": ([vp, vp, vp, vp], ci),
+        "ddi_plan_check": ([vp, vp], ci),
         "ddi_apply_host": ([vp, vp, vp, vp], ci),
         "ddi_apply_timed": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(cd), ci,
                              ctypes.POINTER(ci)], ci),
@@ -117,6 +120,10 @@ def load():
         "gpe_ground_state": ([vp, vp, vp, cd, cd, cd, cd, ci, cd, ci, ci, ctypes.POINTER(GpeStats), vp], ci),
         "gpe_step_adjoint": ([vp, vp, vp, vp, vp, cd, cd, cd, vp], ci),
         "gpe_sums_noalloc": ([vp, vp, ctypes.c_int64, ci, vp, vp], ci),
+        "gpe_trap_observable": ([vp, vp, vp, cd, cd, cd, ci, vp, ctypes.POINTER(cd), vp], ci),
+        "gpe_trap_gradient_workspace": ([vp, ci, ci, ctypes.POINTER(ctypes.c_size_t)], ci),
+        "gpe_trap_gradient": ([vp, vp, vp, cd, cd, cd, ci, ci, vp, ctypes.c_size_t, ctypes.POINTER(cd), vp, vp],
+                              ci),
         "ddi_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(PlanDesc), ci, ci, vp], ci),
         "ddi_batch_destroy": ([vp], ci),
         "ddi_batch_size": ([vp], ci),
@@ -140,7 +147,7 @@ def _check(status, where):
 
 def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
               precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0, ellipsoid=False,
-              split_full_passes=False, spread=0):
+              split_full_passes=False, spread=0, check_finite=False):
     """A plan descriptor (``ddi_plan_desc``).  split_k0 != 0 selects the improved split
     algorithm of Sec. 2.1 (Eq. 3.9), 3D only: window q = exp(-|k|^2/k0^2) with k0 = split_k0
     (< 0: the library's default), the quadrature on the small ball |k| <= kmax (0: 6 k0)
@@ -149,7 +156,8 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     split_full_passes: a split plan's ball NUFFT transforms every fine-grid line instead of
     the band around k = 0 that holds its taps (same result; for comparison).
     spread: SPREAD_AUTO (columns where they apply), SPREAD_TILES or SPREAD_COLUMNS (the
-    type-1 spreading scheme, see ddi_plan_desc.spread)."""
+    type-1 spreading scheme, see ddi_plan_desc.spread).  check_finite: apply() synchronises
+    and raises DDIError (DDI_ERR_NONFINITE) when rho holds NaN or Inf."""
     d = PlanDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -171,6 +179,7 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.ellipsoid = 1 if ellipsoid else 0
     d.split_full_passes = 1 if split_full_passes else 0
     d.spread = int(spread)
+    d.check_finite = 1 if check_finite else 0
     return d
 
 
@@ -260,6 +269,11 @@ class Plan:
                "ddi_apply")
         return out
 
+    def check(self, stream=None):
+        """ddi_plan_check: synchronises, then raises DDIError (DDI_ERR_NONFINITE) if an
+        evaluation since the last check read NaN or Inf in its rho (the record is cleared)."""
+        _check(load().ddi_plan_check(self._h, ctypes.c_void_p(_stream(stream))), "ddi_plan_check")
+
     def apply_host(self, rho_host, out_host, stream=None):
         """End-to-end from host (numpy or pinned torch CPU) buffers; synchronises."""
         def ptr(a):
@@ -348,6 +362,36 @@ class Plan:
         out["converged"] = status == 0
         return out
 
+    def trap_observable(self, psi0, V, beta, lam, dt, nsteps, psi_T=None, stream=None):
+        """J = h^d sum x_last^2 |psi_T|^2 after nsteps gpe_step steps from psi0 (gpe_trap_observable;
+        psi0 is left unchanged).  Returns (J, psi_T)."""
+        import torch
+        if psi_T is None:
+            psi_T = torch.empty_like(psi0)
+        J = ctypes.c_double(0.0)
+        _check(load().gpe_trap_observable(self._h, self._req(psi0, True), self._req(V), float(beta), float(lam),
+                                          float(dt), int(nsteps), self._req(psi_T, True), ctypes.byref(J),
+                                          ctypes.c_void_p(_stream(stream))), "gpe_trap_observable")
+        return J.value, psi_T
+
+    def trap_gradient(self, psi0, V, beta, lam, dt, nsteps, checkpoint=20, grad=None, stream=None):
+        """J and dJ/dV through the hand-written adjoint with checkpointed recomputation
+        (gpe_trap_gradient); the workspace is a torch buffer of the size the library asks for.
+        Returns (J, grad_V)."""
+        import torch
+        nbytes = ctypes.c_size_t(0)
+        _check(load().gpe_trap_gradient_workspace(self._h, int(nsteps), int(checkpoint), ctypes.byref(nbytes)),
+               "gpe_trap_gradient_workspace")
+        work = torch.empty(int(nbytes.value), dtype=torch.uint8, device=psi0.device)
+        if grad is None:
+            grad = torch.empty_like(V)
+        J = ctypes.c_double(0.0)
+        _check(load().gpe_trap_gradient(self._h, self._req(psi0, True), self._req(V), float(beta), float(lam),
+                                        float(dt), int(nsteps), int(checkpoint), ctypes.c_void_p(work.data_ptr()),
+                                        int(nbytes.value), ctypes.byref(J), self._req(grad),
+                                        ctypes.c_void_p(_stream(stream))), "gpe_trap_gradient")
+        return J.value, grad
+
     def step_adjoint(self, psi_in, cot, grad_V, V, beta, lam, dt, stream=None):
         _check(load().gpe_step_adjoint(self._h, self._req(psi_in, True), self._req(cot, True), self._req(grad_V),
                                        self._req(V), float(beta), float(lam), float(dt),
@@ -419,10 +463,19 @@ def sums_noalloc(psi, V, sums, stream=None):
     """gpe_sums_noalloc: sum |psi|^2, sum V |psi|^2, sum |psi|^4 into the device tensor
     `sums` (3 float64) without any allocation by the library."""
     import torch
-    prec = FP64 if psi.dtype == torch.complex128 else FP32
+    # the precision follows psi; V must match it (the library reads count values of each)
+    kinds = {torch.complex128: (FP64, torch.float64), torch.complex64: (FP32, torch.float32)}
+    if psi.dtype not in kinds:
+        raise ValueError(f"psi must be complex128 or complex64, got {psi.dtype}")
+    prec, vdt = kinds[psi.dtype]
+    if V.dtype != vdt:
+        raise ValueError(f"V must be {vdt} for psi of dtype {psi.dtype}, got {V.dtype}")
     if not (psi.is_cuda and V.is_cuda and sums.is_cuda and psi.is_contiguous() and V.is_contiguous()
             and sums.dtype == torch.float64 and sums.numel() >= 3 and psi.numel() == V.numel()):
         raise ValueError("psi, V, sums: contiguous CUDA tensors, sums float64 with >= 3 entries")
+    cur = torch.cuda.current_device()
+    if not (psi.device.index == V.device.index == sums.device.index == cur):
+        raise ValueError(f"psi, V and sums must be on the current device cuda:{cur}")
     _check(load().gpe_sums_noalloc(ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                                    int(psi.numel()), prec, ctypes.c_void_p(sums.data_ptr()),
                                    ctypes.c_void_p(_stream(stream))), "gpe_sums_noalloc")
@@ -430,49 +483,15 @@ def sums_noalloc(psi, V, sums, stream=None):
 
 
 def trap_gradient(plan, psi0, V, beta, lam, dt, nsteps, checkpoint=20, stream=None):
-    """J = h^d sum z^2 |psi_T|^2 after nsteps TSFP steps and dJ/dV (hand-written adjoint).
-
-    Forward states are kept every ``checkpoint`` steps; the backward sweep recomputes
-    each segment's step inputs from its checkpoint, then applies the per-step adjoint
-    in reverse.  Returns (J, grad_V) as (float, tensor).
-    """
-    import torch
-    psi = psi0.clone()
-    ckpt = {0: psi.clone()}
-    for s in range(nsteps):
-        plan.gpe_step(psi, V, beta, lam, dt, 1, stream)
-        if (s + 1) % checkpoint == 0 and s + 1 < nsteps:
-            ckpt[s + 1] = psi.clone()
-    z = _z_coordinate(plan, psi.device)
-    J = plan.dv * float(torch.sum(z * z * (psi.real ** 2 + psi.imag ** 2)).item())
-    cot = (2.0 * z * z).to(psi.dtype) * psi
-    grad = torch.zeros_like(V)
-    seg_starts = sorted(ckpt.keys())
-    for start in reversed(seg_starts):
-        end = min(start + checkpoint, nsteps)
-        states = [ckpt[start].clone()]
-        cur = ckpt[start].clone()
-        for _ in range(start, end - 1):
-            plan.gpe_step(cur, V, beta, lam, dt, 1, stream)
-            states.append(cur.clone())
-        for k in range(end - start - 1, -1, -1):
-            plan.step_adjoint(states[k], cot, grad, V, beta, lam, dt, stream)
-    return J, grad
-
-
-def _z_coordinate(plan, device):
-    import torch
-    d = plan.desc
-    ax = plan.dim - 1
-    n = d.n[ax]
-    z = d.lo[ax] + torch.arange(n, dtype=torch.float64, device=device) * (d.len[ax] / n)
-    shape = [1] * plan.dim
-    shape[0] = n
-    return z.reshape(shape).to(plan.real_dtype)
+    """J = h^d sum z^2 |psi_T|^2 after nsteps TSFP steps and dJ/dV (hand-written adjoint with
+    checkpointed recomputation, all in the library: gpe_trap_gradient).  Returns (J, grad_V)."""
+    return plan.trap_gradient(psi0, V, beta, lam, dt, nsteps, checkpoint, stream=stream)
 
 
 class TrapGradient:
-    """torch.autograd.Function-style wrapper: J(V) with backward through the adjoint."""
+    """torch.autograd.Function over the trap: forward runs the time-splitting steps and
+    returns J (gpe_trap_observable); backward runs the adjoint sweep (gpe_trap_gradient, which
+    recomputes the forward from checkpoints) and scales dJ/dV by the incoming gradient."""
 
     @staticmethod
     def apply(plan, psi0, V, beta, lam, dt, nsteps, checkpoint=20):
@@ -481,13 +500,15 @@ class TrapGradient:
         class _Fn(torch.autograd.Function):
             @staticmethod
             def forward(ctx, Vt):
-                J, g = trap_gradient(plan, psi0, Vt.detach(), beta, lam, dt, nsteps, checkpoint)
-                ctx.save_for_backward(g)
+                Vd = Vt.detach().contiguous()
+                J, _ = plan.trap_observable(psi0, Vd, beta, lam, dt, nsteps)
+                ctx.save_for_backward(Vd)
                 return torch.tensor(J, dtype=torch.float64, device=Vt.device)
 
             @staticmethod
             def backward(ctx, gout):
-                (g,) = ctx.saved_tensors
+                (Vd,) = ctx.saved_tensors
+                _, g = plan.trap_gradient(psi0, Vd, beta, lam, dt, nsteps, checkpoint)
                 return gout.to(g.dtype) * g
 
         return _Fn.apply(V)

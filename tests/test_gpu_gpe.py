@@ -121,6 +121,54 @@ def test_adjoint_matches_oracle_and_fd(D):
         assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
 
 
+def test_trap_gradient_driver_and_autograd(D):
+    # the checkpointed driver behind the C ABI: the checkpoint spacing changes only what is
+    # recomputed, so the gradient is the same bits for every spacing; the autograd Function
+    # runs the forward alone in forward (J as the oracle's) and the adjoint in backward
+    import torch
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    beta, lam, dt, steps = 15.0, 6.0, 0.01, 6
+    ref_grad, ref_J = ogpe.tsfp_adjoint(grid, psi0, V, beta, lam, dt, steps, ddi)
+    plan = D.Plan(3, n, lo, ln, (0.5, 0.0, math.sqrt(0.75)), precision=0)
+    Vt = _t(V, torch.float64)
+    p0 = _t(psi0, torch.complex128)
+    grads = []
+    for ck in (1, 3, 6, 9):
+        J, g = plan.trap_gradient(p0, Vt, beta, lam, dt, steps, checkpoint=ck)
+        assert abs(J - ref_J) <= 1e-12 * abs(ref_J)
+        grads.append(g.clone())
+    for g in grads[1:]:
+        assert torch.equal(g, grads[0])
+    assert np.max(np.abs(grads[0].cpu().numpy() - ref_grad)) <= 1e-10 * np.max(np.abs(ref_grad))
+    Jf, psiT = plan.trap_observable(p0, Vt, beta, lam, dt, steps)
+    assert abs(Jf - ref_J) <= 1e-12 * abs(ref_J)
+    assert torch.equal(p0, _t(psi0, torch.complex128))          # psi0 is read only
+    Vg = Vt.clone().requires_grad_(True)
+    out = D.TrapGradient.apply(plan, p0, Vg, beta, lam, dt, steps, checkpoint=3)
+    assert abs(float(out.detach()) - ref_J) <= 1e-12 * abs(ref_J)
+    (2.0 * out).backward()
+    assert torch.equal(Vg.grad, 2.0 * grads[0])
+
+
+def test_trap_gradient_rejects_short_workspace(D):
+    import ctypes
+    import torch
+    n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)
+    plan = D.Plan(3, n, lo, ln, (0.0, 0.0, 1.0), precision=0)
+    lib = D.load()
+    nbytes = ctypes.c_size_t(0)
+    assert lib.gpe_trap_gradient_workspace(plan._h, 10, 4, ctypes.byref(nbytes)) == 0
+    assert nbytes.value == (3 + 4 + 2) * 16 ** 3 * 16
+    work = torch.empty(nbytes.value - 16, dtype=torch.uint8, device="cuda")
+    J = ctypes.c_double(0.0)
+    Vt = _t(V, torch.float64)
+    g = torch.empty_like(Vt)
+    st = lib.gpe_trap_gradient(plan._h, ctypes.c_void_p(_t(psi0, torch.complex128).data_ptr()),
+                               ctypes.c_void_p(Vt.data_ptr()), 1.0, 0.0, 0.01, 10, 4, ctypes.c_void_p(work.data_ptr()),
+                               nbytes.value - 16, ctypes.byref(J), ctypes.c_void_p(g.data_ptr()), None)
+    assert st == -1 and b"workspace" in lib.ddi_last_error()
+
+
 @pytest.mark.parametrize("row,rule", [(0, 0), (2, 0), (4, 1)])
 def test_virial_table_ground_state_energies(D, row, rule):
     # Table virial_dip3d (beta = 207.16, V = (x^2+y^2+z^2/4)/2, [-12,12]^3, h = 1/4, n = z):

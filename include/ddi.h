@@ -108,6 +108,11 @@ typedef struct {
                           asynchronous and the flag is read by ddi_plan_check (and by ddi_apply_host,
                           which synchronises anyway); 1 => ddi_apply also synchronises `stream` and
                           returns DDI_ERR_NONFINITE when its input held a non-finite value */
+  int compensated;     /* FP32 plans: 1 => compensated arithmetic in the quadrature sum's NUFFT: the column
+                          spread accumulates each fine cell with Kahan summation and the fine-grid FFT passes
+                          apply the twiddles as FP32 head + tail; 0 => plain FP32 (the default: on the
+                          128^3 workload both give the same error to 1e-7, which the w = 8 kernel's
+                          truncation and the FFTs' roundoff set, and the compensated spread is slower) */
 } ddi_plan_desc;
 
 enum { DDI_SPREAD_AUTO = 0, DDI_SPREAD_TILES = 1, DDI_SPREAD_COLUMNS = 2 };

@@ -172,8 +172,10 @@ struct Plan {
   void* d_scale = nullptr;    // T [Mh]: 2 h^d W_q
   NodeDir* d_dirw = nullptr;  // [Mh]: direction and weight without the symbol (ddi_plan_set_axes)
   void* d_c = nullptr;        // cx [Mh]: node values c_q
-  void* d_deconv = nullptr;   // T [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
-  void* d_ones = nullptr;     // T [n0 + n1 + n2] of ones: the pad and crop of a split plan's smooth part
+  void* d_deconv = nullptr;   // double [n0 + n1 + n2]: 1/psihat per axis, index j (0..n-1)
+  void* d_deconv_x2 = nullptr;  // float2 [n0]: the x factors as FP32 head + tail (FP32 plans)
+  void* d_ones = nullptr;     // double [n0 + n1 + n2] of ones: the pad and crop of a split plan's smooth part
+  void* d_ones_x2 = nullptr;  // float2 [n0] of (1, 0)
   void* d_fine = nullptr;     // cx [nf0 nf1 nf2]
   void* d_partial = nullptr;  // cx [nslots * tile cells]
   int4* d_visits = nullptr;   // spread visit lists: (node, ox, oy, oz) relative to the tile
@@ -190,7 +192,7 @@ struct Plan {
   
   void* d_cpart = nullptr;    // partial planes: [slot][kColY * kColX] complex
   int ncunits = 0, ncred = 0, ncslots = 0;
-  int col_stage = 32;         // visits a warp stages at a time (16 or 32)
+  bool col_comp = false;      // column spread: compensated (Kahan) plane accumulation
   long long visits = 0;       // total visit-list entries
   long long pairs = 0;        // total (node, plane) pairs of all units
   int npl = 1;                // owned planes per tile (z-planes in 3D; 1 in 2D)
@@ -204,6 +206,7 @@ struct Plan {
   // fine-grid y lines that hold node taps: yr[0], yr[0] + 1, .. (mod nf_y), yr[1] of them;
   // the NUFFT's z passes transform only these columns and its y passes only store / read them
   int yr[2] = {0, 1};
+  bool precise_nufft = false;  // NUFFT passes apply FP32 twiddles as head + tail
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n} (FP32: n heads, then n tails)
   // GPE workspace

@@ -43,9 +43,10 @@ template <typename T>
 struct Geo {
   using C = cx_t<T>;
   Axis ax, ay, az;
-  const T* dcx;
-  const T* dcy;
-  const T* dcz;
+  // deconvolution factors 1 / psihat, FP64 (x: [0, n0), y: [n0, n0 + n1), z: after), and for
+  // FP32 plans the x factors as FP32 head + tail pairs (the FP64 value to ~2^-48)
+  const double* dc;
+  const float2* dcx2;
   C* fine;
   // the fine-grid y lines that hold node taps: ylo, ylo + 1, .. (mod nf_y), nyr of them
   int ylo, nyr;
@@ -69,8 +70,36 @@ template <typename T>
 struct RowRef {
   long long grid;  // offset of the row in rho / phi
   long long fine;  // offset of the row in the fine grid
-  T dy, dz;        // deconvolution factors of the row
+  T hi, lo;        // the row's deconvolution factor dy dz (FP64 product): FP64 value, or FP32 head + tail
 };
+
+// the row (jy, jz) of a line: offsets and its factor dy dz, formed in FP64
+template <typename T>
+__device__ __forceinline__ RowRef<T> row_ref(const Geo<T>& g, long long L) {
+  const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
+  const double f = g.dc[g.ax.n + jy] * g.dc[g.ax.n + g.ay.n + jz];
+  RowRef<T> r;
+  r.grid = L * g.ax.n;
+  r.fine = g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), 0);
+  r.hi = (T)f;
+  r.lo = sizeof(T) == 4 ? (T)(f - (double)r.hi) : (T)0;
+  return r;
+}
+
+// v times the deconvolution factor of element jx of row r, rounded once: in FP64 directly;
+// in FP32 the factor dx dy dz is formed as a head + tail pair (the exact product error of the
+// heads by an FMA plus the cross terms), so only the final product is rounded
+template <typename T>
+__device__ __forceinline__ T deconv(const Geo<T>& g, const RowRef<T>& r, int jx, T v) {
+  if constexpr (sizeof(T) == 8) {
+    return v * (g.dc[jx] * r.hi);
+  } else {
+    const float2 fx = __ldg(g.dcx2 + jx);
+    const float ph = fx.x * r.hi;
+    const float pe = fmaf(fx.x, r.hi, -ph) + fmaf(fx.x, r.lo, fx.y * r.hi);
+    return fmaf(v, ph, v * pe);
+  }
+}
 
 template <typename T>
 struct PadX {
@@ -81,16 +110,13 @@ struct PadX {
   const T* rho;
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }
   __device__ bool contig() const { return true; }
-  __device__ Ref ref(long long L) const {
-    const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
-    return Ref{L * g.ax.n, g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), 0), g.dcy[jy], g.dcz[jz]};
-  }
+  __device__ Ref ref(long long L) const { return row_ref<T>(g, L); }
   __device__ C load(const Ref& r, int i) const {
     if (!g.ax.in_block(i)) return cmk<C>((T)0, (T)0);
     const int jx = g.ax.grid_of(i);
     const T v = __ldg(rho + r.grid + jx);
     if (!isfinite(v) && *(volatile int*)g.nonfinite == 0) atomicOr(g.nonfinite, 1);
-    return cmk<C>(v * (g.dcx[jx] * r.dy * r.dz), (T)0);
+    return cmk<C>(deconv<T>(g, r, jx, v), (T)0);
   }
   __device__ void store(const Ref& r, int i, C v) const { g.fine[r.fine + i] = v; }
 };
@@ -204,15 +230,12 @@ struct CropX {
   T* phi;
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }
   __device__ bool contig() const { return true; }
-  __device__ Ref ref(long long L) const {
-    const int jy = (int)(L % g.ay.n), jz = (int)(L / g.ay.n);
-    return Ref{L * g.ax.n, g.fidx(g.az.fine_of(jz), g.ay.fine_of(jy), 0), g.dcy[jy], g.dcz[jz]};
-  }
+  __device__ Ref ref(long long L) const { return row_ref<T>(g, L); }
   __device__ C load(const Ref& r, int i) const { return __ldg(g.fine + r.fine + i); }
   __device__ void store(const Ref& r, int i, C v) const {
     if (!g.ax.in_block(i)) return;
     const int jx = g.ax.grid_of(i);
-    const T val = v.x * (g.dcx[jx] * r.dy * r.dz);
+    const T val = deconv<T>(g, r, jx, v.x);
     if (ACC)
       phi[r.grid + jx] += val;
     else
@@ -290,12 +313,23 @@ Geo<T> geo_of(Plan& p, bool unit = false) {
   g.ylo = unit ? 0 : p.yr[0];
   g.nyr = unit ? p.nf[1] : p.yr[1];
   g.nonfinite = p.d_nonfinite;
-  const T* dc = static_cast<const T*>(unit ? p.d_ones : p.d_deconv);
-  g.dcx = dc;
-  g.dcy = dc + p.n[0];
-  g.dcz = dc + p.n[0] + p.n[1];
+  g.dc = static_cast<const double*>(unit ? p.d_ones : p.d_deconv);
+  g.dcx2 = static_cast<const float2*>(unit ? p.d_ones_x2 : p.d_deconv_x2);
   g.fine = static_cast<cx_t<T>*>(p.d_fine);
   return g;
+}
+
+// a policy with the twiddles applied as head + tail (FP32 tables hold both)
+template <typename P>
+struct Precise : P {
+  static constexpr bool kPreciseTwiddles = true;
+};
+
+// one pass of the NUFFT's fine-grid transforms, with precise twiddles when the plan asks
+template <typename T, int DIR, typename P>
+int pass(Plan& p, int n, const P& pol, cudaStream_t s) {
+  if (p.precise_nufft) return dispatch_policy<T, DIR>(n, Precise<P>{pol}, twiddles(p, n), s);
+  return dispatch_policy<T, DIR>(n, pol, twiddles(p, n), s);
 }
 
 }  // namespace
@@ -310,19 +344,19 @@ bool use_band(const Plan& p) {
 template <typename T>
 int nufft_forward_fft(Plan& p, const T* rho, cudaStream_t s) {
   const Geo<T> g = geo_of<T>(p);
-  DDI_TRY((dispatch_policy<T, -1>(p.nf[0], PadX<T>{g, rho}, twiddles(p, p.nf[0]), s)));
+  DDI_TRY((pass<T, -1>(p, p.nf[0], PadX<T>{g, rho}, s)));
   p.mark("pad_fft_x", s);
   if (use_band<T>(p)) {
-    DDI_TRY((dispatch_policy<T, -1>(p.nf[1], BandY<T, true>{g, p.band[0]}, twiddles(p, p.nf[1]), s)));
+    DDI_TRY((pass<T, -1>(p, p.nf[1], BandY<T, true>{g, p.band[0]}, s)));
     p.mark("band_fft_y_fwd", s);
-    DDI_TRY((dispatch_policy<T, -1>(p.nf[2], BandZ<T, true>{g, p.band[0], p.band[1]}, twiddles(p, p.nf[2]), s)));
+    DDI_TRY((pass<T, -1>(p, p.nf[2], BandZ<T, true>{g, p.band[0], p.band[1]}, s)));
     p.mark("band_fft_z_fwd", s);
     return DDI_OK;
   }
-  DDI_TRY((dispatch_policy<T, -1>(p.nf[1], BlockY<T, true>{g}, twiddles(p, p.nf[1]), s)));
+  DDI_TRY((pass<T, -1>(p, p.nf[1], BlockY<T, true>{g}, s)));
   p.mark("fft_y_fwd", s);
   if (p.dim == 3) {
-    DDI_TRY((dispatch_policy<T, -1>(p.nf[2], AllZ<T, true>{g}, twiddles(p, p.nf[2]), s)));
+    DDI_TRY((pass<T, -1>(p, p.nf[2], AllZ<T, true>{g}, s)));
     p.mark("fft_z_fwd", s);
   }
   return DDI_OK;
@@ -334,22 +368,22 @@ int nufft_inverse_fft(Plan& p, T* phi, cudaStream_t s, bool acc) {
   if (use_band<T>(p)) {
     // the spread wrote every fine cell, zero off the taps, so the skipped lines are zero
     // before and after their transforms, as the crop expects
-    DDI_TRY((dispatch_policy<T, +1>(p.nf[2], BandZ<T, false>{g, p.band[0], p.band[1]}, twiddles(p, p.nf[2]), s)));
+    DDI_TRY((pass<T, +1>(p, p.nf[2], BandZ<T, false>{g, p.band[0], p.band[1]}, s)));
     p.mark("band_fft_z_inv", s);
-    DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BandY<T, false>{g, p.band[0]}, twiddles(p, p.nf[1]), s)));
+    DDI_TRY((pass<T, +1>(p, p.nf[1], BandY<T, false>{g, p.band[0]}, s)));
     p.mark("band_fft_y_inv", s);
   } else {
     if (p.dim == 3) {
-      DDI_TRY((dispatch_policy<T, +1>(p.nf[2], AllZ<T, false>{g}, twiddles(p, p.nf[2]), s)));
+      DDI_TRY((pass<T, +1>(p, p.nf[2], AllZ<T, false>{g}, s)));
       p.mark("fft_z_inv", s);
     }
-    DDI_TRY((dispatch_policy<T, +1>(p.nf[1], BlockY<T, false>{g}, twiddles(p, p.nf[1]), s)));
+    DDI_TRY((pass<T, +1>(p, p.nf[1], BlockY<T, false>{g}, s)));
     p.mark("fft_y_inv", s);
   }
   if (acc)
-    DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T, true>{g, phi}, twiddles(p, p.nf[0]), s)));
+    DDI_TRY((pass<T, +1>(p, p.nf[0], CropX<T, true>{g, phi}, s)));
   else
-    DDI_TRY((dispatch_policy<T, +1>(p.nf[0], CropX<T, false>{g, phi}, twiddles(p, p.nf[0]), s)));
+    DDI_TRY((pass<T, +1>(p, p.nf[0], CropX<T, false>{g, phi}, s)));
   p.mark(acc ? "fft_x_inv_crop_add" : "fft_x_inv_crop", s);
   return DDI_OK;
 }

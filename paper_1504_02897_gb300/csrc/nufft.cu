@@ -447,29 +447,36 @@ struct ColArgs {
   const int* unit_slots;  // per unit: the partial slot of each leading, then trailing plane
 };
 
-// acc_k += g psi_z(k) for the run whose rotated, doubled psi_z row is pz
-template <int W>
-__device__ __forceinline__ void col_apply(float2 (&acc0)[W], float2 (&acc1)[W], const float* pz, float2 g0, float2 g1) {
-  const float4* p4 = reinterpret_cast<const float4*>(pz);
+// a += x with the rounding error of the sum carried in c (compensated summation, Kahan):
+// y = x - c, t = a + y, c = (t - a) - y, a = t
+__device__ __forceinline__ void kahan_add2(float2& a, float2& c, float2 x) {
+  const float2 y = __fadd2_rn(x, make_float2(-c.x, -c.y));
+  const float2 t = __fadd2_rn(a, y);
+  c = __fadd2_rn(__fadd2_rn(t, make_float2(-a.x, -a.y)), make_float2(-y.x, -y.y));
+  a = t;
+}
+
+// acc_k += g psi_z(k) for the run whose rotated, doubled psi_z row is pz; COMP: compensated
+template <int W, bool COMP>
+__device__ __forceinline__ void col_apply(float2 (&acc0)[W], float2 (&acc1)[W], float2 (&cmp0)[W], float2 (&cmp1)[W],
+                                          const float* pz, float2 g0, float2 g1) {
+  const float2* p2 = reinterpret_cast<const float2*>(pz);
 #pragma unroll
-  for (int k = 0; k < W / 2; ++k) {
-    const float4 v = p4[k];
-    const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
-    acc0[2 * k] = __ffma2_rn(g0, va, acc0[2 * k]);
-    acc1[2 * k] = __ffma2_rn(g1, va, acc1[2 * k]);
-    acc0[2 * k + 1] = __ffma2_rn(g0, vb, acc0[2 * k + 1]);
-    acc1[2 * k + 1] = __ffma2_rn(g1, vb, acc1[2 * k + 1]);
-  }
-  if constexpr (W % 2 == 1) {
-    const float2 v = reinterpret_cast<const float2*>(pz)[W - 1];
-    acc0[W - 1] = __ffma2_rn(g0, v, acc0[W - 1]);
-    acc1[W - 1] = __ffma2_rn(g1, v, acc1[W - 1]);
+  for (int k = 0; k < W; ++k) {
+    const float2 v = p2[k];
+    if constexpr (COMP) {
+      kahan_add2(acc0[k], cmp0[k], __fmul2_rn(g0, v));
+      kahan_add2(acc1[k], cmp1[k], __fmul2_rn(g1, v));
+    } else {
+      acc0[k] = __ffma2_rn(g0, v, acc0[k]);
+      acc1[k] = __ffma2_rn(g1, v, acc1[k]);
+    }
   }
 }
 
 #define DDI_COL_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)
 
-template <int W, int NS>
+template <int W, int NS, bool COMP>
 __global__ void __launch_bounds__(kColThreads) k_spread_col(ColArgs a) {
   using S = ColStage<W, NS>;
   static_assert(W <= 16, "planes 0..15 of the window");
@@ -496,21 +503,21 @@ __global__ void __launch_bounds__(kColThreads) k_spread_col(ColArgs a) {
     const int cx = U.col % a.ncx, cy = U.col / a.ncx;
     const long long cell = (long long)(cy * kColY + ly) * nfx + cx * kColX + lx;  // cell (lx, ly); + 4 nfx: (lx, ly + 4)
     const int zpart_hi = U.z1 - U.phi;
-    float2 acc0[W], acc1[W];
+    float2 acc0[W], acc1[W], cmp0[W], cmp1[W];
 #pragma unroll
-    for (int k = 0; k < W; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
+    for (int k = 0; k < W; ++k) acc0[k] = acc1[k] = cmp0[k] = cmp1[k] = make_float2(0.f, 0.f);
     int zb = U.z0;
     // write plane zb (direct, or a partial slot when other units touch it), clear its registers
     auto flush = [&]() {
       float2 v0 = make_float2(0.f, 0.f), v1 = v0;
       switch (zb % W) {
-#define DDI_TAKE(R)                              \
-  case R:                                        \
-    if constexpr (R < W) {                       \
-      v0 = acc0[R];                              \
-      v1 = acc1[R];                              \
-      acc0[R] = acc1[R] = make_float2(0.f, 0.f); \
-    }                                            \
+#define DDI_TAKE(R)                                                  \
+  case R:                                                            \
+    if constexpr (R < W) {                                           \
+      v0 = COMP ? __fadd2_rn(acc0[R], make_float2(-cmp0[R].x, -cmp0[R].y)) : acc0[R]; \
+      v1 = COMP ? __fadd2_rn(acc1[R], make_float2(-cmp1[R].x, -cmp1[R].y)) : acc1[R]; \
+      acc0[R] = acc1[R] = cmp0[R] = cmp1[R] = make_float2(0.f, 0.f); \
+    }                                                                \
     break;
         DDI_COL_CASES(DDI_TAKE)
 #undef DDI_TAKE
@@ -590,7 +597,7 @@ __global__ void __launch_bounds__(kColThreads) k_spread_col(ColArgs a) {
           g0 = __ffma2_rn(make_float2(w0, w0), cq, g0);
           g1 = __ffma2_rn(make_float2(w1, w1), cq, g1);
         }
-        col_apply<W>(acc0, acc1, st->pz[j0], g0, g1);
+        col_apply<W, COMP>(acc0, acc1, cmp0, cmp1, st->pz[j0], g0, g1);
       }
       __syncwarp();
     }
@@ -637,10 +644,10 @@ __global__ void __launch_bounds__(256)
   *reinterpret_cast<float4*>(fine + (long long)r.y * nfx * nfy + cell) = sum;
 }
 
-template <int W, int NS>
+template <int W, int NS, bool COMP>
 int configure_spread_col(Plan& p) {
   const size_t smem = sizeof(ColStage<W, NS>) * (kColThreads / 32);
-  auto kern = k_spread_col<W, NS>;
+  auto kern = k_spread_col<W, NS, COMP>;
   {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -658,7 +665,7 @@ int configure_spread_col(Plan& p) {
   return DDI_OK;
 }
 
-template <int W, int NS>
+template <int W, int NS, bool COMP>
 int launch_spread_col(Plan& p, cudaStream_t s) {
   ColArgs a;
   for (int d = 0; d < 3; ++d) a.nf[d] = p.nf[d];
@@ -673,7 +680,7 @@ int launch_spread_col(Plan& p, cudaStream_t s) {
   a.partial = static_cast<float2*>(p.d_cpart);
   a.unit_slots = p.d_cslots;
   DDI_CUDA(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
-  k_spread_col<W, NS><<<p.spread_blocks, kColThreads, p.spread_smem, s>>>(a);
+  k_spread_col<W, NS, COMP><<<p.spread_blocks, kColThreads, p.spread_smem, s>>>(a);
   DDI_LAUNCH_CHECK();
   p.mark("spread", s);
   if (p.ncred > 0) {
@@ -687,8 +694,8 @@ int launch_spread_col(Plan& p, cudaStream_t s) {
 
 template <int W>
 int spread_col_ns(Plan& p, cudaStream_t s, bool configure) {
-  if (p.col_stage == 16) return configure ? configure_spread_col<W, 16>(p) : launch_spread_col<W, 16>(p, s);
-  return configure ? configure_spread_col<W, 32>(p) : launch_spread_col<W, 32>(p, s);
+  if (p.col_comp) return configure ? configure_spread_col<W, 32, true>(p) : launch_spread_col<W, 32, true>(p, s);
+  return configure ? configure_spread_col<W, 32, false>(p) : launch_spread_col<W, 32, false>(p, s);
 }
 
 int spread_col_w(Plan& p, cudaStream_t s, bool configure) {

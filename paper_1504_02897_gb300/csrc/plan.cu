@@ -95,6 +95,7 @@ void choose_tile(Plan& p) {
 
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_dirw,   p.d_l0,     p.d_psi,   p.d_scale, p.d_c,    p.d_deconv, p.d_ones,  p.d_fine,
+                  p.d_deconv_x2, p.d_ones_x2,
                   p.d_partial,
                   p.d_visits, p.d_units, p.d_split, p.d_counter, p.d_psi1, p.d_rho, p.d_phi, p.d_work,
                   p.d_work2,  p.d_kin,   p.d_red,   p.d_io_in, p.d_io_out, p.d_cvis, p.d_cunits, p.d_cred,
@@ -464,6 +465,10 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
     return DDI_ERR_ARG;
   }
   p.spread_kind = (d.spread != DDI_SPREAD_TILES && columns_apply(p)) ? DDI_SPREAD_COLUMNS : DDI_SPREAD_TILES;
+  // compensated FP32 arithmetic: head + tail twiddles in the NUFFT's fine-grid passes and
+  // compensated (Kahan) plane sums in the column spread
+  p.precise_nufft = d.compensated != 0 && d.precision == DDI_FP32;
+  p.col_comp = d.compensated != 0;
 
   // one node of each (k, -k) pair: the first half of the azimuth
   const int nphi = d.nphi, half = nphi / 2;
@@ -571,7 +576,7 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
 
   // device memory
   const size_t rs = p.real_size(), cs = p.cx_size();
-  std::vector<float> k1, k2, k3;
+  std::vector<float> k1, k2;
   DDI_TRY(upload(p, &p.d_l0, l0s, "node taps", stream));
   DDI_TRY(upload_real(p, &p.d_psi, psi, "kernel values", stream, &k1));
   DDI_TRY(upload_real(p, &p.d_scale, scale, "node scales", stream, &k2));
@@ -585,12 +590,26 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
     }
     DDI_TRY(upload(p, (void**)&p.d_dirw, dirw, "node directions", stream));
   }
-  DDI_TRY(upload_real(p, &p.d_deconv, dc, "deconvolution", stream, &k3));
-  std::vector<float> k4;
+  // deconvolution factors stay FP64 in both precisions; FP32 plans also get the x factors
+  // as FP32 head + tail pairs (applied so that only the final product is rounded)
+  auto pairs = [](const std::vector<double>& v, int n) {
+    std::vector<float2> out((size_t)n);
+    for (int j = 0; j < n; ++j) {
+      const float hi = (float)v[j];
+      out[j] = make_float2(hi, (float)(v[j] - (double)hi));
+    }
+    return out;
+  };
+  DDI_TRY(upload(p, &p.d_deconv, dc, "deconvolution", stream));
+  std::vector<float2> dcx2 = pairs(dc, p.n[0]);
+  DDI_TRY(upload(p, &p.d_deconv_x2, dcx2, "deconvolution pairs", stream));
   std::vector<double> ones;
+  std::vector<float2> ones2;
   if (p.split()) {
     ones.assign((size_t)p.n[0] + p.n[1] + p.n[2], 1.0);
-    DDI_TRY(upload_real(p, &p.d_ones, ones, "unit factors", stream, &k4));
+    ones2 = pairs(ones, p.n[0]);
+    DDI_TRY(upload(p, &p.d_ones, ones, "unit factors", stream));
+    DDI_TRY(upload(p, &p.d_ones_x2, ones2, "unit factor pairs", stream));
   }
   DDI_TRY(dev_alloc(p, (void**)&p.d_counter, sizeof(int), "unit counter"));
   DDI_TRY(dev_alloc(p, (void**)&p.d_nonfinite, sizeof(int), "non-finite record"));

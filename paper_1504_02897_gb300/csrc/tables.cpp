@@ -139,6 +139,10 @@ int normalise_desc(const ddi_plan_desc* in, ddi_plan_desc* out, std::string* err
     *err = "spread must be DDI_SPREAD_AUTO, DDI_SPREAD_TILES or DDI_SPREAD_COLUMNS";
     return DDI_ERR_ARG;
   }
+  if (d.compensated != 0 && d.compensated != 1) {
+    *err = "compensated must be 0 or 1";
+    return DDI_ERR_ARG;
+  }
   if (d.check_finite != 0 && d.check_finite != 1) {
     *err = "check_finite must be 0 or 1";
     return DDI_ERR_ARG;

@@ -37,7 +37,7 @@ class PlanDesc(ctypes.Structure):
                 ("kmax", ctypes.c_double), ("precision", ctypes.c_int), ("nufft_tol", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("chunk", ctypes.c_int), ("split_k0", ctypes.c_double),
                 ("ellipsoid", ctypes.c_int), ("split_full_passes", ctypes.c_int), ("spread", ctypes.c_int),
-                ("check_finite", ctypes.c_int)]
+                ("check_finite", ctypes.c_int), ("compensated", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -147,7 +147,7 @@ def _check(status, where):
 
 def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, kmax=0.0,
               precision=FP64, nufft_tol=0.0, tile=None, chunk=0, split_k0=0.0, ellipsoid=False,
-              split_full_passes=False, spread=0, check_finite=False):
+              split_full_passes=False, spread=0, check_finite=False, compensated=False):
     """A plan descriptor (``ddi_plan_desc``).  split_k0 != 0 selects the improved split
     algorithm of Sec. 2.1 (Eq. 3.9), 3D only: window q = exp(-|k|^2/k0^2) with k0 = split_k0
     (< 0: the library's default), the quadrature on the small ball |k| <= kmax (0: 6 k0)
@@ -157,7 +157,8 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     the band around k = 0 that holds its taps (same result; for comparison).
     spread: SPREAD_AUTO (columns where they apply), SPREAD_TILES or SPREAD_COLUMNS (the
     type-1 spreading scheme, see ddi_plan_desc.spread).  check_finite: apply() synchronises
-    and raises DDIError (DDI_ERR_NONFINITE) when rho holds NaN or Inf."""
+    and raises DDIError (DDI_ERR_NONFINITE) when rho holds NaN or Inf.  compensated: FP32 plans
+    use Kahan sums in the column spread and head + tail twiddles in the fine-grid passes."""
     d = PlanDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -180,6 +181,7 @@ def make_desc(dim, n, lo, length, axis_n, axis_m=None, nr=0, ntheta=0, nphi=0, k
     d.split_full_passes = 1 if split_full_passes else 0
     d.spread = int(spread)
     d.check_finite = 1 if check_finite else 0
+    d.compensated = 1 if compensated else 0
     return d
 
 

@@ -17,15 +17,24 @@ pytestmark = pytest.mark.gpu
 TOL = {0: 1e-12, 1: 1e-6}
 
 
-def fp32_floor(it, ref):
-    """Relative change of the exact sum when the density is rounded to FP32 (the FP32
-    path's input), by the oracle.  In 2D the weights grow like |k| up to R = pi/h, so
-    this alone is 3e-7 .. 1.2e-6 of max|Phi| for the 128^2 batched densities and grows
-    with N; the FP32 path (input/deconvolution, forward FFT and interpolation, spread and
-    inverse FFT, each rounding at that level) is held to 8x it when that exceeds 1e-6."""
+def fp32_reference(it, ref):
+    """The oracle on the density rounded to FP32 (what the FP32 path receives) and the
+    input-rounding floor |Phi(rho32) - Phi(rho)| / max|Phi(rho)|.  FP32 items are compared
+    with the rounded-input oracle.  In 3D the symbol is bounded (|Uhat| <= 2) and the FP32
+    path stays below 1e-6 of it.  In 2D the weights grow like |k| up to R = pi/h: white
+    rounding noise of relative size 2^-24 anywhere before the weights (the input itself,
+    which the floor measures, but also the FP32 deconvolution product and the forward FFT's
+    roundoff, which have the same white spectrum) is amplified by ~R, so the FP32 path's own
+    error after removing the input rounding is a multiple of the floor (measured 2.2-2.7 x;
+    the floor grows with N: 4.6e-7 at 128^2, 1.2e-6 at 256^2, 2.3e-6 at 512^2): 2D items are
+    held to max(1e-6, 4 x floor)."""
     t = qd.plan_tables(len(it["n"]), it["n"], it["len"], it["axis"])
     r32 = nudft.ddi(it["rho"].astype(np.float32).astype(np.float64), t, it["n"], it["lo"], it["len"])
-    return _relinf(r32, ref)
+    return r32, _relinf(r32, ref)
+
+
+def fp32_tol(it, floor):
+    return TOL[1] if len(it["n"]) == 3 else max(TOL[1], 4.0 * floor)
 
 
 @pytest.fixture(scope="module")
@@ -86,10 +95,12 @@ def test_batch_mixed_matches_oracle(D, graph):
     for i, (it, d, o) in enumerate(zip(items, descs, outs)):
         assert b.infos[i].spread_tuned_ms > 0.0
         ref = _oracle(it)
-        err = _relinf(o.double().cpu().numpy(), ref)
         tol = TOL[d.precision]
-        if d.precision == 1 and len(it["n"]) == 2:
-            tol = max(tol, 8.0 * fp32_floor(it, ref))
+        if d.precision == 1:
+            ref, floor = fp32_reference(it, ref)
+            tol = fp32_tol(it, floor)
+        err = _relinf(o.double().cpu().numpy(), ref)
+        print(f"[batch item {i} n={it['n']} prec={d.precision}] rel err {err:.3e} (tol {tol:.1e})")
         assert err <= tol, (i, it["n"], d.precision, err)
     b.close()
 
@@ -181,7 +192,8 @@ def test_autotuned_plan_and_cache(D):
     got = p1.apply(torch.from_numpy(rho).to("cuda", torch.float32))
     torch.cuda.synchronize()
     t = qd.plan_tables(3, n, ln, (0.0, 0.6, 0.8))
-    assert _relinf(got.double().cpu().numpy(), nudft.ddi(rho, t, n, lo, ln)) <= TOL[1]
+    ref = nudft.ddi(rho.astype(np.float32).astype(np.float64), t, n, lo, ln)
+    assert _relinf(got.double().cpu().numpy(), ref) <= TOL[1]
     n2, lo2, ln2 = synth.box(N, 11.0, 3)
     p2 = D.Plan(3, n2, lo2, ln2, (1.0, 0.0, 0.0), precision=1, tile=(-1, 0, 0))
     assert tuple(p2.info.tile) == tuple(p1.info.tile)
@@ -211,8 +223,8 @@ def test_batch_96_densities_2d(D):
     # the batched 2D workload: 96 densities, N in {128, 256, 512, 1024}, box length
     # U[8, 16], tilt U[0, 90] degrees, 4 Gaussians each, quadrature 2N x 2N, FP32,
     # autotuned tiles, one recorded graph.  Oracle parity on a subset (every size the
-    # oracle finishes in seconds: four 128^2 items and one 256^2 item), to 1e-6 or 8x
-    # the item's FP32 input-rounding floor, whichever is larger.
+    # oracle finishes in seconds: four 128^2 items and one 256^2 item), against the oracle
+    # on the FP32-rounded density (fp32_reference, fp32_tol).
     import torch
     items = synth.batch_2d(count=96, seed=0)
     descs = [_desc(D, it, precision=1) for it in items]
@@ -226,8 +238,10 @@ def test_batch_96_densities_2d(D):
     small = [i for i, it in enumerate(items) if it["n"][0] == 128][:4]
     small += [i for i, it in enumerate(items) if it["n"][0] == 256][:1]
     for i in small:
-        ref = _oracle(items[i])
+        ref, floor = fp32_reference(items[i], _oracle(items[i]))
         err = _relinf(outs[i].double().cpu().numpy(), ref)
-        floor = fp32_floor(items[i], ref)
-        assert err <= max(TOL[1], 8.0 * floor), (i, items[i]["n"], err, floor)
+        tol = fp32_tol(items[i], floor)
+        print(f"[batch96 item {i} n={items[i]['n']}] rel err {err:.3e} vs rounded input (floor {floor:.2e}, "
+              f"tol {tol:.1e})")
+        assert err <= tol, (i, items[i]["n"], err, floor)
     b.close()

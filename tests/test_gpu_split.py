@@ -82,11 +82,12 @@ def test_split_matches_oracle(D, name, precision):
     ref = split.ddi_split(c["rho"], c["n"], c["lo"], c["ln"], c["axis"], c["m"], k0=c["k0"], **c["sizes"])
     tol = TOL[precision]
     if precision:
-        # the FP32 path cannot beat the rounding of its input: 8x that floor where it exceeds 1e-6
-        r32 = split.ddi_split(c["rho"].astype(np.float32).astype(np.float64), c["n"], c["lo"], c["ln"], c["axis"],
+        # FP32: against the oracle on the FP32-rounded density, the input the path receives
+        ref = split.ddi_split(c["rho"].astype(np.float32).astype(np.float64), c["n"], c["lo"], c["ln"], c["axis"],
                               c["m"], k0=c["k0"], **c["sizes"])
-        tol = max(tol, 8.0 * _relinf(r32, ref))
-    assert _relinf(got, ref) <= tol
+    err = _relinf(got, ref)
+    print(f"[split {name} prec={precision}] rel err {err:.3e} (tol {tol:.1e})")
+    assert err <= tol
 
 
 def test_split_parts_through_the_stages(D):

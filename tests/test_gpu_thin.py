@@ -66,9 +66,17 @@ def test_thin_box_matches_oracle(D, name, precision):
     ref = nudft.ddi(rho, t, n, lo, ln)
     tol = 1e-12
     if precision:
+        # FP32: against the oracle on the FP32-rounded density (what the path receives); in
+        # 2D the symbol grows like |k| (here up to pi/h_y = 50), so white rounding noise before
+        # the weights (the FP32 deconvolution product, the forward FFT) is amplified like the
+        # input rounding: max(1e-6, 4 x the input-rounding floor), see tests/test_gpu_batch.py
         r32 = nudft.ddi(rho.astype(np.float32).astype(np.float64), t, n, lo, ln)
-        tol = max(1e-6, 8.0 * _relinf(r32, ref))
-    assert _relinf(got, ref) <= tol
+        floor = _relinf(r32, ref)
+        ref = r32
+        tol = 1e-6 if dim == 3 else max(1e-6, 4.0 * floor)
+    err = _relinf(got, ref)
+    print(f"[thin {name} prec={precision}] rel err {err:.3e} (tol {tol:.1e})")
+    assert err <= tol
 
 
 def test_thin_box_set_axes_equals_fresh_plan(D):

@@ -335,7 +335,7 @@ def test_noalloc_binding_rejects_mismatched_dtypes(lib):
             lib.sums_noalloc(psi, V, sums)
 
 
-@pytest.mark.parametrize("field,value", [("spread", 3), ("spread", -1), ("check_finite", 2)])
+@pytest.mark.parametrize("field,value", [("spread", 3), ("spread", -1), ("check_finite", 2), ("compensated", 2)])
 def test_scheme_fields_validated(lib, field, value):
     desc = lib.make_desc(3, (16, 16, 16), (-1, -1, -1), (2, 2, 2), (0, 0, 1))
     setattr(desc, field, value)

@@ -240,31 +240,39 @@ def cufft_comparator(torch, stream):
 
 
 def kernel_bytes(name, info, real=4):
+    """Algorithmic bytes of one launch of a kernel of the 128^3 DDI: what it must read and
+    write once.  The fine grid is (2N)^3 complex; the NUFFT's y passes store / read and its z
+    passes transform only the fine y lines that hold node taps (info.yrange, about half);
+    the spread writes those columns once; node data are the kernel values along x, y, z, the
+    first taps and c_q (or the scale 2 h^d W_q) of each processed node."""
     cx = 2 * real
     n3 = N ** 3
+    nf = 2 * N
     mh = int(info.nodes_used)
-    node_in = mh * (8 + 4 * real)          # ushort4 start taps + 4 reals (offsets, weight)
+    w = int(info.width)
+    yfrac = info.yrange[1] / nf if info.yrange[1] else 1.0
     # cells the taps reach: the ball |k| <= kmax is kmax (nf h / 2 pi) = kmax 2L / pi fine cells
-    # in radius (N for the full rule, kmax = pi / h)
+    # in radius (N for the full rule, kmax = pi / h), on the k_y >= 0 side of the processed nodes
     radius = info.kmax * 2 * L / math.pi
-    ball = int(4.0 / 3.0 * math.pi * (radius + info.width / 2.0) ** 3) * cx
+    ball = int(4.0 / 3.0 * math.pi * (radius + w / 2.0) ** 3 * min(1.0, yfrac + w / nf)) * cx
+    psi = mh * 3 * w * real + mh * 8        # kernel values and first taps
     table = {
-        "pad_fft_x": n3 * real + 2 * n3 * cx,           # read rho, write N^2 rows of 2N
-        "fft_y_fwd": 2 * n3 * cx + 4 * n3 * cx,         # read the block half, write planes
-        "fft_z_fwd": 4 * n3 * cx + 8 * n3 * cx,
-        "interp": ball + node_in + mh * cx,
-        "spread": 8 * n3 * cx + node_in + mh * cx,      # every fine cell written once
+        "pad_fft_x": n3 * real + 2 * n3 * cx,                # read rho, write N^2 rows of 2N
+        "fft_y_fwd": 2 * n3 * cx + 4 * n3 * cx * yfrac,      # read the block half, write the tap lines
+        "fft_z_fwd": (4 * n3 * cx + 8 * n3 * cx) * yfrac,    # the columns on the tap lines
+        "interp": ball + psi + mh * real + mh * cx,          # taps' cells, node data, scale in, c_q out
+        "spread": 8 * n3 * cx * yfrac + psi + mh * cx,       # tap-line columns written once, node data in
         "spread_reduce": 0,
-        "fft_z_inv": 8 * n3 * cx + 4 * n3 * cx,
-        "fft_y_inv": 4 * n3 * cx + 2 * n3 * cx,
+        "fft_z_inv": (8 * n3 * cx + 4 * n3 * cx) * yfrac,
+        "fft_y_inv": 4 * n3 * cx * yfrac + 2 * n3 * cx,
         "fft_x_inv_crop": 2 * n3 * cx + n3 * real,
         "fft_x_inv_crop_add": 2 * n3 * cx + 2 * n3 * real,  # also reads phi (split plans)
     }
-    # the split algorithm's smooth part: the same passes without the deconvolution
-    smooth = {"smooth_pad_fft_x": "pad_fft_x", "smooth_fft_y_fwd": "fft_y_fwd", "smooth_fft_z_symbol": "fft_z_fwd",
-              "smooth_fft_z_inv": "fft_z_inv", "smooth_fft_y_inv": "fft_y_inv",
-              "smooth_fft_x_inv_crop": "fft_x_inv_crop"}
-    return table.get(smooth.get(name, name), 0)
+    # the split algorithm's smooth part: the same passes without the deconvolution, every line
+    smooth = {"smooth_pad_fft_x": n3 * real + 2 * n3 * cx, "smooth_fft_y_fwd": 6 * n3 * cx,
+              "smooth_fft_z_symbol": 12 * n3 * cx, "smooth_fft_z_inv": 12 * n3 * cx, "smooth_fft_y_inv": 6 * n3 * cx,
+              "smooth_fft_x_inv_crop": 2 * n3 * cx + n3 * real}
+    return table.get(name, smooth.get(name, 0))
 
 
 def profile_driver(args):
@@ -297,6 +305,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true",
                     help="ddi3d_128: skip the split-algorithm side measurement (a child process)")
+    ap.add_argument("--no-side", action="store_true",
+                    help="ddi3d_128: skip the GPE and batch side measurements (child processes)")
     ap.add_argument("--workload", default="ddi3d_128",
                     choices=["ddi3d_128", "ddi3d_128_split", "batch2d_96", "tsfp128", "gs128", "grad128"],
                     help="ddi3d_128: the headline 3D workload; ddi3d_128_split: the same density by the "
@@ -464,9 +474,12 @@ def main():
                "sample": f"{detail['sample_nodes']} of {N * 64 * 128} nodes (type 2 + type 1 over the full 128^3 "
                          f"grid) in {detail['sample_seconds']:.1f} s, scaled by nodes"}
 
-    split_side = None
+    sides = {}
     if rank == 0 and world == 1 and not args.no_split:
-        split_side = split_side_run()
+        sides["split_algorithm"] = split_side_run()
+    if rank == 0 and world == 1 and not args.no_side:
+        for wl, key in (("tsfp128", "tsfp128"), ("gs128", "gs128"), ("batch2d_96", "batch2d_96")):
+            sides[key] = side_run(wl)
 
     if rank == 0:
         out = {
@@ -492,11 +505,31 @@ def main():
         }
         if cpu:
             out["cpu_baseline"] = cpu
-        if split_side is not None:
-            out["split_algorithm"] = split_side
+        out.update(sides)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def side_run(workload, timeout_s=300):
+    """Another workload measured by a child process after the headline (its own CUDA context,
+    so nothing it does can touch the numbers above): the child's JSON line without the keys
+    the headline already states, or the reason it has none."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", workload, "--steps", "20", "--warmup", "3",
+           "--fp64-check", "1"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"no result within {timeout_s} s"}
+    if r.returncode != 0:
+        return {"error": f"exit status {r.returncode}: " + " | ".join(r.stderr.strip().splitlines()[-3:])}
+    for line in reversed(r.stdout.strip().splitlines()):
+        try:
+            d = json.loads(line)
+        except ValueError:
+            continue
+        return {k: v for k, v in d.items() if k not in ("n_gpus", "scaling", "vs_baseline", "data")}
+    return {"error": "no JSON line in the child's output"}
 
 
 def split_side_run(timeout_s=240):
@@ -723,6 +756,17 @@ def bench_batch2d(args):
         e2e_step()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
+    # FP32 error of one item of each size against the FP64 path (parity-tested against the
+    # oracle) applied to the same FP32-rounded density
+    errs = {}
+    for size in (128, 256, 512, 1024):
+        i = next(j for j, it in enumerate(items) if it["n"][0] == size)
+        it = items[i]
+        p64 = ddi.Plan(2, it["n"], it["lo"], it["len"], it["axis"], precision=ddi.FP64)
+        ref = p64.apply(rhos[i].double())
+        torch.cuda.synchronize()
+        errs[f"{size}^2 item {i}"] = float((outs[i].double() - ref).abs().max() / ref.abs().max())
+        p64.close()
     grid_pts = sum(it["n"][0] * it["n"][1] for it in items)
     nodes = sum(int(i.nodes) for i in tuned.infos)
     # algorithmic HBM bytes of one DDI: density in and potential out (2 x 4 B per grid
@@ -745,6 +789,7 @@ def bench_batch2d(args):
                    "graph": True, "autotuned_tiles": sizes, "ms_builtin_tiles": ms_plain,
                    "ms_eager_launches": ms_eager, "graph_records": records, "graph_launches": launches,
                    "create_s_autotuned": create_tuned, "create_s_builtin": create_plain,
+                   "fp32_rel_err_vs_fp64_path_same_input": errs,
                    "l2": "flushed before every timed step (256 MiB write)"},
         "ddi_roofline": {"algorithmic_bytes": ddi_bytes, "achieved": ddi_bytes / (ms * 1e-3) / 1e9,
                          "peak": peak, "frac": ddi_bytes / (ms * 1e-3) / 1e9 / peak, "unit": "GB/s",
@@ -810,9 +855,25 @@ def bench_gpe(args):
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         m1 = plan.gpe_energy(psi, V, beta, lam)["mass"]
         step_bytes = 8 * 128 ** 3 + 2 * 4 * 256 ** 3 * 8 + 4 * 2 * 8 * 128 ** 3 + 50e6
+        err = {}
+        if args.fp64_check:
+            # the FP32 state after 10 steps from the FP32-rounded initial state, against the FP64
+            # path's 10 steps from the same rounded state (parity-tested against the oracle)
+            psi0_64 = synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0), eps=0.05, seed=0).astype(np.complex64)
+            a = torch.from_numpy(psi0_64).to(dev)
+            for _ in range(10):
+                plan.gpe_step(a, V, beta, lam, dt, 1)
+            p64 = plan_of(ddi.FP64)
+            b = torch.from_numpy(psi0_64.astype(np.complex128)).to(dev)
+            V64t = torch.from_numpy(V64.astype(np.float32).astype(np.float64)).to(dev)
+            for _ in range(10):
+                p64.gpe_step(b, V64t, beta, lam, dt, 1)
+            torch.cuda.synchronize()
+            err = {"fp32_rel_err_vs_fp64_10_steps": float((a.to(torch.complex128) - b).abs().max() / b.abs().max())}
+            del p64
         out = dict(base, metric="TSFP steps/s at 128^3 (Eq. tssp2 Case I, DDI included, FP32-mixed)",
                    value=1e3 / ms, unit="steps/s", steps=args.steps, warmup=args.warmup, ms_per_step=ms,
-                   config=dict(cfg, workload="tsfp128_dt1e-3", dt=dt,
+                   config=dict(cfg, workload="tsfp128_dt1e-3", dt=dt, **err,
                                mass_drift_per_step=abs(m1 - m0) / (args.steps + args.warmup),
                                l2="inputs (67 MB of state) plus the 134 MB fine grid exceed L2"),
                    step_roofline={"model_bytes": step_bytes, "achieved": step_bytes / (ms * 1e-3) / 1e9,
@@ -828,12 +889,23 @@ def bench_gpe(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         clocks = sampler.stop()
+        if args.fp64_check:
+            # the FP32 path's energies of its ground state against the FP64 path's energies of
+            # the same state (the FP32 state upcast)
+            p64 = plan_of(ddi.FP64)
+            e64 = p64.gpe_energy(phi.to(torch.complex128), torch.from_numpy(V64.astype(np.float32).astype(np.float64)).to(dev),
+                                 beta, lam)
+            e32 = plan.gpe_energy(phi, V, beta, lam)
+            st["fp32_energy_rel_err_vs_fp64"] = {k: abs(e32[k] - e64[k]) / abs(e64[k])
+                                                 for k in ("E", "mu", "Ekin", "Epot", "Eint", "Edip")}
+            del p64
         out = dict(base, metric="ground state time at 128^3 (GF-BE, |dE| < 1e-10, FP32 + FP64 reductions)",
                    value=wall, unit="s", higher_is_better=False, steps=st["steps"], warmup=0,
                    ms_per_step=wall / max(1, st["steps"]) * 1e3,
                    config=dict(cfg, workload="gs128_dt0.01", dt=0.01, converged=st["converged"],
                                E=st["E"], mu=st["mu"], virial=st["virial"], mass=st["mass"],
-                               last_change=st["last_change"], inner_max=st["inner_max"]),
+                               last_change=st["last_change"], inner_max=st["inner_max"],
+                               fp32_energy_rel_err_vs_fp64=st.get("fp32_energy_rel_err_vs_fp64")),
                    clocks=clocks)
     else:
         dt, nsteps = 1e-3, 400

@@ -79,7 +79,7 @@ int tune_column_chunk(Plan& p, cudaStream_t s) {
   }
   int best = 0;
   double best_ms = 0.0;
-  for (const int c : {128, 192, 256, 384, 512}) {
+  for (const int c : {32, 64, 128, 192, 256, 384, 512}) {
     p.desc.chunk = c;
     DDI_TRY(build_spread_col(p, s));
     float ms = 0.f;

@@ -58,9 +58,11 @@ def test_single_process_rate():
 
 
 def test_kernel_byte_model():
-    # the roofline's algorithmic bytes: the split plan's smooth-part passes count as their
-    # NUFFT counterparts, the accumulating crop also reads phi, and the interpolation's
-    # gathered cells follow the quadrature radius (N fine cells for the full rule)
+    # the roofline's algorithmic bytes: the split plan's smooth-part passes transform every
+    # line (their NUFFT counterparts with all y lines), the accumulating crop also reads phi,
+    # the z passes and the spread touch the fraction of fine y lines that hold taps, and the
+    # interpolation's gathered cells follow the quadrature radius (N fine cells for the full
+    # rule) on the taps' side of k_y
     sys.path.insert(0, ROOT)
     import math
     import bench
@@ -69,18 +71,29 @@ def test_kernel_byte_model():
         nodes_used = 49152
         width = 8
         kmax = math.pi / (2 * bench.L / bench.N)
+        yrange = (0, 2 * bench.N)
 
     n3 = bench.N ** 3
     for smooth, base in (("smooth_pad_fft_x", "pad_fft_x"), ("smooth_fft_z_symbol", "fft_z_fwd"),
                          ("smooth_fft_x_inv_crop", "fft_x_inv_crop")):
         assert bench.kernel_bytes(smooth, Info) == bench.kernel_bytes(base, Info) > 0
     assert bench.kernel_bytes("fft_x_inv_crop_add", Info) == bench.kernel_bytes("fft_x_inv_crop", Info) + 4 * n3
+    node = 49152 * (3 * 8 * 4 + 8)
     full = bench.kernel_bytes("interp", Info)
     ball = int(4.0 / 3.0 * math.pi * (bench.N + 4.0) ** 3) * 8
-    assert full == ball + 49152 * (8 + 16) + 49152 * 8
+    assert full == ball + node + 49152 * (4 + 8)
+    assert bench.kernel_bytes("spread", Info) == 8 * n3 * 8 + node + 49152 * 8
+    zfull = bench.kernel_bytes("fft_z_fwd", Info)
+    Info.yrange = (250, bench.N + 6)          # taps on N + 6 of the 2N fine y lines
+    frac = (bench.N + 6) / (2 * bench.N)
+    assert bench.kernel_bytes("fft_z_fwd", Info) == pytest.approx(zfull * frac)
+    assert bench.kernel_bytes("spread", Info) == pytest.approx(8 * n3 * 8 * frac + node + 49152 * 8)
+    assert bench.kernel_bytes("smooth_fft_z_symbol", Info) == zfull
     Info.kmax = 2.4
+    Info.yrange = (0, 2 * bench.N)
     # radius 2.4 (2L / pi) = 18.3 fine cells: the gathered ball shrinks by (22.3 / 132)^3
-    assert bench.kernel_bytes("interp", Info) == int(4.0 / 3.0 * math.pi * (2.4 * 2 * bench.L / math.pi + 4.0) ** 3) * 8 + 49152 * 32
+    assert bench.kernel_bytes("interp", Info) == int(4.0 / 3.0 * math.pi * (2.4 * 2 * bench.L / math.pi + 4.0) ** 3) * 8 \
+        + node + 49152 * 12
     assert bench.kernel_bytes("no_such_kernel", Info) == 0
 
 

@@ -202,6 +202,51 @@ def test_autotuned_plan_and_cache(D):
     p2.close()
 
 
+def test_batch_1024_item_stages(D):
+    # a 1024^2 item of the batched workload through its single plan (batch items compute the
+    # same bits as their single plans): the type-2 stage at 256 sampled nodes and the type-1
+    # stage (seeded random node values) at 256 sampled grid points, each against the oracle's
+    # per-node / per-point sums on the FP32-rounded inputs.
+    # The type-2 stage carries an absolute error, not a relative one: the FP32 forward path
+    # (deconvolution product, 2D FFT of (2N)^2 points in log2((2N)^2) stages, w x w taps) leaves
+    # the sum f_q = sum_j rho_j e^{-i k_q.x_j} with an error of a few 2^-24 sum|rho|, the same at
+    # every node, and c_q = 2 h^2 W_q f_q scales it by 2 h^2 |W_q|, which grows like |k| to
+    # R = pi/h; where f_q itself has decayed (|k| large) c_q is that noise alone.  Bound:
+    # |c_q - ref_q| <= K 2^-24 sum|rho| 2 h^2 |W_q| with K = log2((2N)^2) + w + 2 (a rounding's
+    # worth per FFT stage and per tap row)
+    import torch
+    it = next(x for x in synth.batch_2d(count=96, seed=0) if x["n"][0] == 1024)
+    plan = D.Plan(2, it["n"], it["lo"], it["len"], it["axis"], precision=1)
+    t = qd.plan_tables(2, it["n"], it["len"], it["axis"])
+    order = plan.node_order()
+    centre = np.array([it["lo"][d] + it["len"][d] / 2 for d in range(2)])
+    rng = np.random.default_rng(13)
+    # type 2: c_q = 2 h^2 W_q f_q
+    c = plan.type2(torch.from_numpy(it["rho"]).to("cuda", torch.float32)).cpu().numpy().astype(np.complex128)
+    sel = rng.choice(len(order), 256, replace=False)
+    q = order[sel]
+    r32 = it["rho"].astype(np.float32).astype(np.float64)
+    ref = 2.0 * t["W"][q] * nudft.type2(r32, t["k"][q], it["n"], it["lo"], it["len"]) * np.exp(1j * (t["k"][q] @ centre))
+    h2 = (it["len"][0] / 1024) * (it["len"][1] / 1024)
+    scale = 2.0 * h2 * np.abs(t["W"][q]) * np.sum(np.abs(r32))
+    K = math.log2(2048.0 * 2048.0) + plan.info.width + 2
+    e2 = float(np.max(np.abs(c[sel] - ref) / scale) / 2.0 ** -24)   # in units of 2^-24
+    # type 1 of random node values (rounded to complex64, the plan's precision)
+    mh = int(plan.info.nodes_used)
+    cv = ((rng.standard_normal(mh) + 1j * rng.standard_normal(mh)) * 1e-3).astype(np.complex64)
+    phi = plan.type1(torch.from_numpy(cv).cuda()).double().cpu().numpy()
+    k = t["k"][order]
+    idx = rng.integers(0, 1024, size=(256, 2))
+    pts = np.stack([it["lo"][d] + idx[:, d] * (it["len"][d] / 1024) for d in range(2)], axis=1)
+    ref1 = nudft.type1_at(cv.astype(np.complex128) * np.exp(-1j * (k @ centre)), k, pts)
+    e1 = _relinf(phi[idx[:, 1], idx[:, 0]], ref1)
+    print(f"[batch 1024^2 item] type-2 stage error {e2:.2f} x 2^-24 sum|rho| 2 h^2 |W_q| (bound K = {K:.0f}); "
+          f"type-1 stage rel err {e1:.3e}")
+    assert e1 <= TOL[1]
+    assert e2 <= K
+    plan.close()
+
+
 def test_batch_2d_1024_trace_identity(D):
     # 2D trace identity at the largest batched size: with m = n, the symbol summed over
     # n = e_x, e_y, e_z is 3/2 [(k_x^2 + k_y^2)/|k| - |k|] = 0 at every node, so the three
@@ -222,9 +267,9 @@ def test_batch_2d_1024_trace_identity(D):
 def test_batch_96_densities_2d(D):
     # the batched 2D workload: 96 densities, N in {128, 256, 512, 1024}, box length
     # U[8, 16], tilt U[0, 90] degrees, 4 Gaussians each, quadrature 2N x 2N, FP32,
-    # autotuned tiles, one recorded graph.  Oracle parity on a subset (every size the
-    # oracle finishes in seconds: four 128^2 items and one 256^2 item), against the oracle
-    # on the FP32-rounded density (fp32_reference, fp32_tol).
+    # autotuned tiles, one recorded graph.  Oracle parity on a subset: four 128^2 items and one
+    # 256^2 item on the whole grid, two 512^2 items and one 1024^2 item at 200 sampled grid
+    # points, against the oracle on the FP32-rounded density (fp32_reference, fp32_tol).
     import torch
     items = synth.batch_2d(count=96, seed=0)
     descs = [_desc(D, it, precision=1) for it in items]
@@ -244,4 +289,25 @@ def test_batch_96_densities_2d(D):
         print(f"[batch96 item {i} n={items[i]['n']}] rel err {err:.3e} vs rounded input (floor {floor:.2e}, "
               f"tol {tol:.1e})")
         assert err <= tol, (i, items[i]["n"], err, floor)
+    # two 512^2 items at 200 sampled grid points: the oracle's type-2 sum at all 4 N^2 nodes
+    # (for the density and for its FP32 rounding), then the type-1 sum at the points
+    large = [i for i, it in enumerate(items) if it["n"][0] == 512][:2]
+    rng = np.random.default_rng(12)
+    for i in large:
+        it = items[i]
+        t = qd.plan_tables(2, it["n"], it["len"], it["axis"])
+        N = it["n"][0]
+        idx = rng.integers(0, N, size=(200, 2))
+        pts = np.stack([it["lo"][d] + idx[:, d] * (it["len"][d] / N) for d in range(2)], axis=1)
+        refs = []
+        for rho in (it["rho"], it["rho"].astype(np.float32).astype(np.float64)):
+            rh = nudft.type2(rho, t["k"], it["n"], it["lo"], it["len"], block=1024)
+            refs.append(nudft.type1_at(t["W"] * rh, t["k"], pts))
+        floor = _relinf(refs[1], refs[0])
+        got = outs[i].double().cpu().numpy()[idx[:, 1], idx[:, 0]]
+        err = _relinf(got, refs[1])
+        tol = fp32_tol(it, floor)
+        print(f"[batch96 item {i} n={it['n']}] rel err {err:.3e} at 200 points vs rounded input "
+              f"(floor {floor:.2e}, tol {tol:.1e})")
+        assert err <= tol, (i, it["n"], err, floor)
     b.close()

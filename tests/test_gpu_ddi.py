@@ -298,8 +298,13 @@ def test_full_size_ddi_sampled_points(D, full_ref, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_size_type2_sampled_nodes(D, full_ref, precision):
-    # stage check: c_q = 2 h^3 W_q f_q at 3000 sampled nodes (FP32: against the type-2 sum of
-    # the FP32-rounded density at those nodes)
+    # stage check: c_q = 2 h^3 W_q f_q at 3000 sampled nodes.  FP64: relative 1e-12.  FP32:
+    # against the type-2 sum of the FP32-rounded density, with an absolute bound: the FP32
+    # forward path (deconvolution product, FFT of (2N)^3 points in log2((2N)^3) stages, w^3 taps)
+    # leaves f_q = sum_j rho_j e^{-i k_q.x_j} with an error of a few 2^-24 sum|rho| at every node,
+    # and c_q scales it by 2 h^3 |W_q|, which carries the Jacobian |k|^2; where f_q has decayed
+    # (|k| large) c_q is that noise alone, so no relative bound holds node by node.  Bound:
+    # |c_q - ref_q| <= K 2^-24 sum|rho| 2 h^3 |W_q|, K = log2((2N)^3) + w + 2
     import torch
     w, sizes, t, rh = full_ref
     plan = _plan(D, 3, w["n"], w["lo"], w["len"], w["axis"], precision=precision, **sizes)
@@ -311,8 +316,18 @@ def test_full_size_type2_sampled_nodes(D, full_ref, precision):
     centre = np.array([w["lo"][d] + w["len"][d] / 2 for d in range(3)])
     rq = rh[q] if precision == 0 else nudft.type2(_in(w["rho"], 1), t["k"][q], w["n"], w["lo"], w["len"], block=512)
     ref = 2.0 * t["W"][q] * rq * np.exp(1j * (t["k"][q] @ centre))
-    err = np.max(np.abs(c[sel] - ref)) / np.max(np.abs(ref))
-    assert _report("128^3 type-2 stage", precision, err) <= TOL[precision], err
+    if precision == 0:
+        err = np.max(np.abs(c[sel] - ref)) / np.max(np.abs(ref))
+        assert _report("128^3 type-2 stage", precision, err) <= TOL[precision], err
+    else:
+        h3 = float(np.prod([w["len"][d] / 128 for d in range(3)]))
+        bound = 2.0 * h3 * np.abs(t["W"][q]) * np.sum(np.abs(_in(w["rho"], 1))) * 2.0 ** -24
+        K = math.log2(256.0 ** 3) + plan.info.width + 2
+        ratio = float(np.max(np.abs(c[sel] - ref) / bound))
+        rel = float(np.max(np.abs(c[sel] - ref)) / np.max(np.abs(ref)))
+        print(f"[128^3 type-2 stage prec=1] error {ratio:.2f} x 2^-24 sum|rho| 2 h^3 |W_q| (bound K = {K:.0f}); "
+              f"relative to max |c| {rel:.2e}")
+        assert ratio <= K
 
 
 @pytest.mark.parametrize("precision", [0, 1])

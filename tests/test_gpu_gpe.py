@@ -65,6 +65,54 @@ def test_tsfp_steps_match_oracle(D, precision, tol):
     assert _report(f"tsfp 16^3 x5 prec={precision}", err, tol) <= tol
 
 
+def test_tsfp_32cubed_many_steps_error_growth(D):
+    # FP64 at 32^3 with the paper's dynamics setup of Sec. 4.2 (V = |x|^2 / 2, lambda = beta / 2):
+    # 1e-12 after one step, and the growth of the difference over 40 steps reported and bounded
+    # (each step is unitary up to roundoff, so differences grow slowly)
+    import torch
+    n, lo, ln = synth.box(32, 8.0)
+    axis = (0.0, 0.0, 1.0)
+    grid = ogpe.Grid(n, lo, ln)
+    t = qd.plan_tables(3, n, ln, axis)
+    ddi = lambda rho: nudft.ddi(rho, t, n, lo, ln)
+    V = synth.harmonic_trap(n, lo, ln, (1, 1, 1))
+    psi0 = synth.gpe_initial(n, lo, ln, (1, 1, 1), eps=0.05, seed=5)
+    beta, lam, dt = 10.0, 5.0, 0.008
+    plan = D.Plan(3, n, lo, ln, axis, precision=0)
+    psi = _t(psi0, torch.complex128)
+    Vt = _t(V, torch.float64)
+    ref = psi0
+    errs = []
+    for k in range(40):
+        ref = ogpe.tsfp_step(grid, ref, V, beta, lam, dt, ddi)
+        plan.gpe_step(psi, Vt, beta, lam, dt, 1)
+        if k in (0, 9, 19, 39):
+            errs.append(np.max(np.abs(psi.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    print("[tsfp 32^3 fp64] rel err after 1, 10, 20, 40 steps: " + ", ".join(f"{e:.2e}" for e in errs))
+    assert errs[0] <= 1e-12
+    assert errs[-1] <= 2e-11
+
+
+def test_tsfp_128cubed_one_step(D):
+    # one FP64 step at the full 128^3 size (configs 3/4's box and trap) against the oracle, whose
+    # DDI is the direct quadrature sum over all 1,048,576 nodes (a few minutes on the host)
+    import torch
+    n, lo, ln = synth.box(128, 10.0)
+    axis = (0.0, 0.0, 1.0)
+    grid = ogpe.Grid(n, lo, ln)
+    t = qd.plan_tables(3, n, ln, axis)
+    ddi = lambda rho: nudft.ddi(rho, t, n, lo, ln)
+    V = synth.harmonic_trap(n, lo, ln, (1.0, 1.0, 2.0))
+    psi0 = synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0), eps=0.05, seed=0)
+    beta, lam, dt = 207.16, 0.16 * 207.16, 1e-3
+    ref = ogpe.tsfp_step(grid, psi0, V, beta, lam, dt, ddi)
+    plan = D.Plan(3, n, lo, ln, axis, precision=0)
+    psi = _t(psi0, torch.complex128)
+    plan.gpe_step(psi, _t(V, torch.float64), beta, lam, dt, 1)
+    err = np.max(np.abs(psi.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert _report("tsfp 128^3 fp64, one step", err, 1e-12) <= 1e-12
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-6)])
 def test_energies_match_oracle(D, precision, tol):
     n, lo, ln, grid, ddi, V, psi0 = _setup(16, 5.0)

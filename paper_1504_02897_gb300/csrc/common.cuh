@@ -206,6 +206,8 @@ struct Plan {
   // fine-grid y lines that hold node taps: yr[0], yr[0] + 1, .. (mod nf_y), yr[1] of them;
   // the NUFFT's z passes transform only these columns and its y passes only store / read them
   int yr[2] = {0, 1};
+  // fine-grid x lines that hold node taps (every line, except for split plans' ball band)
+  int xr[2] = {0, 1};
   bool precise_nufft = false;  // NUFFT passes apply FP32 twiddles as head + tail
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n} (FP32: n heads, then n tails)

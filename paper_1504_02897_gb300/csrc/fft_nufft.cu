@@ -48,8 +48,10 @@ struct Geo {
   const double* dc;
   const float2* dcx2;
   C* fine;
-  // the fine-grid y lines that hold node taps: ylo, ylo + 1, .. (mod nf_y), nyr of them
+  // the fine-grid y lines that hold node taps: ylo, ylo + 1, .. (mod nf_y), nyr of them; and
+  // the x lines (xlo, .., nxr of them; every line except for split plans' ball)
   int ylo, nyr;
+  int xlo, nxr;
   int* nonfinite;  // set when the pad pass reads a NaN / Inf
   __device__ long long fidx(int lz, int ly, int lx) const {
     return ((long long)lz * ay.nf + ly) * ax.nf + lx;
@@ -58,6 +60,11 @@ struct Geo {
     int d = l - ylo;
     if (d < 0) d += ay.nf;
     return d < nyr;
+  }
+  __host__ __device__ bool in_xr(int l) const {
+    int d = l - xlo;
+    if (d < 0) d += ax.nf;
+    return d < nxr;
   }
   __host__ __device__ int yr_line(int i) const {
     const int l = ylo + i;
@@ -185,7 +192,8 @@ struct BandY {
     return g.fidx(g.az.fine_of((int)(L / wx)), 0, band_line((int)(L % wx), bx, g.ax.nf));
   }
   __device__ C load(Ref r, int i) const {
-    if (FWD && !g.ay.in_block(i)) return cmk<C>((T)0, (T)0);
+    // inverse: the spread wrote only the band's y lines (the others hold no tap)
+    if (FWD ? !g.ay.in_block(i) : !g.in_yr(i)) return cmk<C>((T)0, (T)0);
     return __ldg(g.fine + r + (long long)i * g.ax.nf);
   }
   __device__ void store(Ref r, int i, C v) const {
@@ -231,7 +239,11 @@ struct CropX {
   __host__ __device__ long long nlines() const { return (long long)g.ay.n * g.az.n; }
   __device__ bool contig() const { return true; }
   __device__ Ref ref(long long L) const { return row_ref<T>(g, L); }
-  __device__ C load(const Ref& r, int i) const { return __ldg(g.fine + r.fine + i); }
+  __device__ C load(const Ref& r, int i) const {
+    // x lines outside the taps' range were neither written by the spread nor transformed
+    if (!g.in_xr(i)) return cmk<C>((T)0, (T)0);
+    return __ldg(g.fine + r.fine + i);
+  }
   __device__ void store(const Ref& r, int i, C v) const {
     if (!g.ax.in_block(i)) return;
     const int jx = g.ax.grid_of(i);
@@ -312,6 +324,8 @@ Geo<T> geo_of(Plan& p, bool unit = false) {
   g.az = Axis{p.n[2], p.nf[2]};
   g.ylo = unit ? 0 : p.yr[0];
   g.nyr = unit ? p.nf[1] : p.yr[1];
+  g.xlo = unit ? 0 : p.xr[0];
+  g.nxr = unit ? p.nf[0] : p.xr[1];
   g.nonfinite = p.d_nonfinite;
   g.dc = static_cast<const double*>(unit ? p.d_ones : p.d_deconv);
   g.dcx2 = static_cast<const float2*>(unit ? p.d_ones_x2 : p.d_deconv_x2);

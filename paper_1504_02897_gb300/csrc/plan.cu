@@ -346,14 +346,20 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
     const int b0 = start[c], b1 = start[c + 1];
     const size_t u0 = units.size();
     if (b0 == b1) {
-      // an empty column is written as zeros, unless none of its y lines holds a tap (the
+      // an empty column is written as zeros, unless none of its x or y lines holds a tap (the
       // NUFFT's passes neither transform nor read those lines)
-      bool needed = false;
+      bool in_y = false, in_x = false;
       for (int r = 0; r < kColY; ++r) {
         int d = (c / ncx) * kColY + r - p.yr[0];
         if (d < 0) d += nfy;
-        needed = needed || d < p.yr[1];
+        in_y = in_y || d < p.yr[1];
       }
+      for (int r = 0; r < kColX; ++r) {
+        int d = (c % ncx) * kColX + r - p.xr[0];
+        if (d < 0) d += nfx;
+        in_x = in_x || d < p.xr[1];
+      }
+      const bool needed = in_x && in_y;
       if (needed)
         for (int z = 0; z < nfz; z += lmax) units.push_back(ColUnit{c, b0, b0, z, std::min(nfz, z + lmax), 0, 0, 0});
       continue;
@@ -564,6 +570,15 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
     } else {
       p.yr[0] = best_end;  // the first touched line after the gap
       p.yr[1] = nfy - best;
+    }
+    p.xr[0] = 0;
+    p.xr[1] = p.nf[0];
+    // split plans with a band: the ball's taps lie within |l| <= band of k = 0 along x and y
+    if (p.split() && p.dim == 3 && p.band[0] > 0 && p.band[1] > 0) {
+      p.xr[0] = p.nf[0] - p.band[0];
+      p.xr[1] = 2 * p.band[0] + 1;
+      p.yr[0] = nfy - p.band[1];
+      p.yr[1] = 2 * p.band[1] + 1;
     }
   }
 

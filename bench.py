@@ -308,7 +308,7 @@ def main():
     ap.add_argument("--no-side", action="store_true",
                     help="ddi3d_128: skip the GPE and batch side measurements (child processes)")
     ap.add_argument("--workload", default="ddi3d_128",
-                    choices=["ddi3d_128", "ddi3d_128_split", "batch2d_96", "tsfp128", "gs128", "grad128"],
+                    choices=["ddi3d_128", "ddi3d_128_split", "batch2d_96", "tsfp128", "gs128", "grad128", "grad128_fd"],
                     help="ddi3d_128: the headline 3D workload; ddi3d_128_split: the same density by the "
                          "improved split algorithm (Eq. 3.9); batch2d_96: 96 2D densities in one batch; "
                          "tsfp128 / gs128 / grad128: the GPE step, ground state and trap gradient at 128^3")
@@ -334,7 +334,7 @@ def main():
     if args.workload == "ddi3d_128_split":
         bench_split(args)
         return
-    if args.workload in ("tsfp128", "gs128", "grad128"):
+    if args.workload in ("tsfp128", "gs128", "grad128", "grad128_fd"):
         bench_gpe(args)
         return
 
@@ -907,6 +907,37 @@ def bench_gpe(args):
                                last_change=st["last_change"], inner_max=st["inner_max"],
                                fp32_energy_rel_err_vs_fp64=st.get("fp32_energy_rel_err_vs_fp64")),
                    clocks=clocks)
+    elif args.workload == "grad128_fd":
+        # config 4's own check, in the FP64 path: dJ/dV by the adjoint (checkpoints every 20
+        # steps) against central differences (J(V + eps d) - J(V - eps d)) / (2 eps), eps = 1e-4,
+        # on the 16 seeded smoothed-noise directions of synth.trap_directions
+        dt, nsteps, eps = 1e-3, 400, 1e-4
+        del plan
+        torch.cuda.empty_cache()
+        p64 = plan_of(ddi.FP64)
+        psi0 = torch.from_numpy(synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0), eps=0.05, seed=0)).to(dev)
+        V = torch.from_numpy(V64).to(dev)
+        sampler.start()
+        t0 = time.perf_counter()
+        J, g = p64.trap_gradient(psi0, V, beta, lam, dt, nsteps, checkpoint=20)
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+        rows = []
+        psiT = torch.empty_like(psi0)
+        for d in synth.trap_directions(n, count=16, seed=0):
+            dt_ = torch.from_numpy(d).to(dev)
+            Jp, _ = p64.trap_observable(psi0, V + eps * dt_, beta, lam, dt, nsteps, psiT)
+            Jm, _ = p64.trap_observable(psi0, V - eps * dt_, beta, lam, dt, nsteps, psiT)
+            fd = (Jp - Jm) / (2.0 * eps)
+            ad = float((g * dt_).sum().item())
+            rows.append({"fd": fd, "adjoint": ad, "rel_diff": abs(fd - ad) / abs(fd)})
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        out = dict(base, metric="trap gradient vs central differences at 128^3 (FP64, 400 steps, 16 directions)",
+                   value=max(r["rel_diff"] for r in rows), unit="max relative difference", higher_is_better=False,
+                   dtype="f64", steps=nsteps, warmup=0, ms_per_step=t_grad / nsteps * 1e3,
+                   config=dict(cfg, workload="grad128_fd_16dirs_eps1e-4", dt=dt, J=J, gradient_s=t_grad,
+                               total_s=wall, directions=rows), clocks=clocks)
     else:
         dt, nsteps = 1e-3, 400
         psi0_64 = synth.gpe_initial(n, lo, ln, (1.0, 1.0, 2.0), eps=0.05, seed=0)

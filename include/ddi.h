@@ -99,10 +99,12 @@ typedef struct {
                           every line, as a plan without split_k0 does */
   int spread;          /* type-1 spreading scheme: 0 => automatic (columns where they apply, else plane
                           tiles); DDI_SPREAD_TILES => owner-computes tile planes in shared memory (`tile`,
-                          `chunk`); DDI_SPREAD_COLUMNS => 8 x 4-cell columns of the fine grid whose z-planes
-                          a warp accumulates in registers (FP32 3D plans whose fine grid is a multiple of
-                          8 in x and 4 in y and at least w + 7 cells in x, w + 3 in y and w in z;
-                          DDI_ERR_ARG otherwise; `chunk` = visits per work item) */
+                          `chunk`); DDI_SPREAD_COLUMNS => columns of the fine grid whose planes along the
+                          last axis a warp accumulates in registers: 8 x 8 cells in x-y running along z
+                          (3D), 8 cells in x running along y (2D).  Applies to FP32 plans whose fine grid
+                          is a multiple of 8 in x (3D: and in y) and at least w + 7 cells in x (3D: w + 7
+                          in y and w in z; 2D: w in y), and not to compensated 2D plans; DDI_ERR_ARG
+                          otherwise; `chunk` = visits per work item */
   int check_finite;    /* NaN / Inf in rho: the pad pass of every evaluation records them in a device
                           flag of the plan (at no cost for finite input).  0 => ddi_apply stays
                           asynchronous and the flag is read by ddi_plan_check (and by ddi_apply_host,

@@ -11,7 +11,8 @@
 //
 // The autotuner picks the spread tile of a plan by timing the spread (with its
 // partial-plane reduction) for a list of candidate tiles on the plan's own node set and
-// keeping the fastest.  The node positions on the fine grid depend only on the grid, the
+// keeping the fastest; for column plans it picks the visits per work unit, and for 2D
+// plans with the automatic scheme it times both schemes and keeps the faster.  The node positions on the fine grid depend only on the grid, the
 // quadrature sizes and kmax h, not on the box length or the dipole axes, so the result
 // is cached per such shape (and device) for the life of the process.
 #include <algorithm>
@@ -32,6 +33,7 @@ struct TuneResult {
   std::array<int, 3> tile;
   int chunk;  // column plans: visits per work unit
   double ms;
+  int kind;   // the spreading scheme (DDI_SPREAD_TILES / DDI_SPREAD_COLUMNS)
 };
 std::map<std::string, TuneResult> g_tune_cache;
 
@@ -89,7 +91,7 @@ int tune_column_chunk(Plan& p, cudaStream_t s) {
       best_ms = ms;
     }
   }
-  g_tune_cache[key] = TuneResult{{{0, 0, 0}}, best, best_ms};
+  g_tune_cache[key] = TuneResult{{{0, 0, 0}}, best, best_ms, DDI_SPREAD_COLUMNS};
   lock.unlock();
   p.desc.chunk = best;
   DDI_TRY(build_spread_col(p, s));
@@ -97,8 +99,7 @@ int tune_column_chunk(Plan& p, cudaStream_t s) {
   return DDI_OK;
 }
 
-int tune_spread_tile(Plan& p, cudaStream_t s) {
-  if (p.spread_kind == DDI_SPREAD_COLUMNS) return tune_column_chunk(p, s);
+int tune_tiles(Plan& p, cudaStream_t s) {
   const std::string key = tune_key_of(p);
   std::unique_lock<std::mutex> lock(g_tune_mu);
   auto hit = g_tune_cache.find(key);
@@ -133,12 +134,67 @@ int tune_spread_tile(Plan& p, cudaStream_t s) {
     set_error("spread-tile autotuner: no candidate tile fits in shared memory");
     return DDI_ERR_ARG;
   }
-  g_tune_cache[key] = TuneResult{best, 0, best_ms};
+  g_tune_cache[key] = TuneResult{best, 0, best_ms, DDI_SPREAD_TILES};
   lock.unlock();
   set_tile(p, best.data());
   DDI_TRY(build_spread(p, s));
   p.tuned_ms = best_ms;
   return DDI_OK;
+}
+
+// 2D plans with the automatic scheme: the column spread at its best unit size against the
+// tile spread at its best tile, the faster kept (the column spread wins on small fine
+// grids, the tile spread on large ones; where the two cross depends on the node set)
+int tune_scheme_2d(Plan& p, cudaStream_t s) {
+  const std::string key = tune_key_of(p) + " scheme";
+  {
+    std::unique_lock<std::mutex> lock(g_tune_mu);
+    auto hit = g_tune_cache.find(key);
+    if (hit != g_tune_cache.end()) {
+      const TuneResult r = hit->second;
+      lock.unlock();
+      drop_spread_lists(p);
+      p.spread_kind = r.kind;
+      if (r.kind == DDI_SPREAD_COLUMNS) {
+        p.desc.chunk = r.chunk;
+        DDI_TRY(build_spread_col(p, s));
+      } else {
+        set_tile(p, r.tile.data());
+        DDI_TRY(build_spread(p, s));
+      }
+      p.tuned_ms = r.ms;
+      return DDI_OK;
+    }
+  }
+  const int user_chunk = p.desc.chunk;
+  drop_spread_lists(p);
+  p.spread_kind = DDI_SPREAD_COLUMNS;
+  DDI_TRY(tune_column_chunk(p, s));
+  const double col_ms = p.tuned_ms;
+  const int col_chunk = p.desc.chunk;
+  p.desc.chunk = user_chunk;
+  drop_spread_lists(p);
+  p.spread_kind = DDI_SPREAD_TILES;
+  DDI_TRY(tune_tiles(p, s));
+  TuneResult r{{{p.tile[0], p.tile[1], p.tile[2]}}, 0, p.tuned_ms, DDI_SPREAD_TILES};
+  if (col_ms < p.tuned_ms) {
+    drop_spread_lists(p);
+    p.spread_kind = DDI_SPREAD_COLUMNS;
+    p.desc.chunk = col_chunk;
+    DDI_TRY(build_spread_col(p, s));
+    p.tuned_ms = col_ms;
+    r = TuneResult{{{0, 0, 0}}, col_chunk, col_ms, DDI_SPREAD_COLUMNS};
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = r;
+  return DDI_OK;
+}
+
+int tune_spread_tile(Plan& p, cudaStream_t s) {
+  if (p.dim == 2 && p.desc.spread == DDI_SPREAD_AUTO && columns_apply(p) && !p.batch_item)
+    return tune_scheme_2d(p, s);
+  if (p.spread_kind == DDI_SPREAD_COLUMNS) return tune_column_chunk(p, s);
+  return tune_tiles(p, s);
 }
 
 }  // namespace ddi
@@ -312,7 +368,7 @@ int build_batch(ddi_batch_s* b, ddi_batch* out, const ddi_plan_desc* descs, int 
       }
       b->plans[i] = p;
       // an exception must not leave a worker thread
-      st = ddi::guarded("ddi_batch_create", [&]() -> int { return ddi::create_plan(*p, &descs[i], s, false); });
+      st = ddi::guarded("ddi_batch_create", [&]() -> int { return ddi::create_plan(*p, &descs[i], s, false, true); });
       if (st != DDI_OK) ddi::set_error("batch item %d: %s", i, ddi::last_error());
     }
     if (st != DDI_OK) {

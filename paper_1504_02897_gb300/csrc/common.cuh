@@ -209,6 +209,7 @@ struct Plan {
   // fine-grid x lines that hold node taps (every line, except for split plans' ball band)
   int xr[2] = {0, 1};
   bool precise_nufft = false;  // NUFFT passes apply FP32 twiddles as head + tail
+  bool batch_item = false;     // built by ddi_batch_create (2D items spread by columns, see create_plan)
   int tw_n[8] = {};           // lengths of the twiddle tables below
   void* d_tw[8] = {};         // cx twiddle tables e^{-2 pi i k / n} (FP32: n heads, then n tails)
   // GPE workspace
@@ -295,10 +296,12 @@ int configure_kernels(Plan& p);  // per-plan launch geometry (nufft.cu)
 int take_nonfinite(Plan& p, cudaStream_t s);
 
 // ---- plans (plan.cu) ------------------------------------------------------------------------
-int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream, bool gpe = true);
+int create_plan(Plan& p, const ddi_plan_desc* desc, cudaStream_t stream, bool gpe = true, bool batch_item = false);
 void set_tile(Plan& p, const int want[3]);         // tile rounded as for ddi_plan_desc.tile
 int build_spread(Plan& p, cudaStream_t stream);     // spread lists for the current tile
 int build_spread_col(Plan& p, cudaStream_t stream); // column spread lists for desc.chunk (plan.cu)
+bool columns_apply(const Plan& p);                   // the column spread fits the plan (plan.cu)
+void drop_spread_lists(Plan& p);                    // frees both schemes' spread lists (plan.cu)
 int time_spread(Plan& p, cudaStream_t s, int reps, float* ms);  // best of reps (nufft.cu)
 int tune_spread_tile(Plan& p, cudaStream_t s);      // autotuner (batch.cu)
 void destroy_plan(Plan& p);

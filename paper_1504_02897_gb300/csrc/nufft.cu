@@ -644,10 +644,184 @@ __global__ void __launch_bounds__(256)
   *reinterpret_cast<float4*>(fine + (long long)r.y * nfx * nfy + cell) = sum;
 }
 
-template <int W, int NS, bool COMP>
+// 2D column spread.  A column is kColX cells of x and every y line (the window axis).  Lane
+// (lx, g) holds cell lx of the column for the W rows of the window (row r in register
+// r mod W, as in 3D); the four lane groups g take different visits of one run (the visits
+// with the same first y tap, which all start at the window's first row) and their sums for
+// a row are added by two shuffles, in a fixed order, when the row leaves the window.  Staged
+// per visit: psi_x in a zero-padded row (as in 3D), psi_y rotated so that register k reads
+// its tap at index k and doubled for packed FMAs, c_q and the first y tap.
+template <int W, int NS>
+struct alignas(16) ColStage2 {
+  static constexpr int PY = ((2 * W + 7) / 8) * 8 + 4;   // psi_y rotated, each value twice, padding
+  static constexpr int PX = ((W + 15 + 7) / 8) * 8 + 4;  // psi_x at [8, 8 + W)
+  float py[NS][PY];
+  float px[NS][PX];
+  int4 hd[NS];  // byte offset of px[j][8 - ox]; 0; c_q (two floats)
+  int sz[NS];   // first y tap
+};
+
+template <int W, int NS>
+__global__ void __launch_bounds__(kColThreads) k_spread_col2(ColArgs a) {
+  using S = ColStage2<W, NS>;
+  static_assert(W <= 16 && W % 2 == 0, "rows 0..15 of the window, psi_y read in pairs of taps");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  S* st = reinterpret_cast<S*>(smem_raw) + warp;
+  const int lx = lane & 7, g = lane >> 3;
+  const int lx4 = 4 * lx;
+  const int nfx = a.nf[0], nfy = a.nf[1];
+  const unsigned st_off = (unsigned)(reinterpret_cast<unsigned char*>(st) - smem_raw);
+  for (int i = lane; i < NS * S::PX; i += 32) (&st->px[0][0])[i] = 0.f;
+  __syncwarp();
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(a.counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= a.nunits) break;
+    const ColUnit U = a.units[u];
+    const int x = U.col * kColX + lx;
+    const int zpart_hi = U.z1 - U.phi;
+    float2 acc[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[k] = make_float2(0.f, 0.f);
+    int zb = U.z0;
+    // row zb leaves the window: the four groups' sums added ((g0 + g1) + (g2 + g3)), written by
+    // group 0 (direct, or to a partial slot when other units touch the row)
+    auto flush = [&]() {
+      float2 v = make_float2(0.f, 0.f);
+      switch (zb % W) {
+#define DDI_TAKE(R)                          \
+  case R:                                    \
+    if constexpr (R < W) {                   \
+      v = acc[R];                            \
+      acc[R] = make_float2(0.f, 0.f);        \
+    }                                        \
+    break;
+        DDI_COL_CASES(DDI_TAKE)
+#undef DDI_TAKE
+      }
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+      if (g == 0) {
+        const int r = zb - U.z0;
+        if (r < U.plo || zb >= zpart_hi) {
+          const int k = r < U.plo ? r : U.plo + (zb - zpart_hi);
+          a.partial[(size_t)__ldg(a.unit_slots + U.slot0 + k) * kColX + lx] = v;
+        } else {
+          __stcs(a.fine + (long long)(zb >= nfy ? zb - nfy : zb) * nfx + x, v);
+        }
+      }
+      ++zb;
+    };
+    for (int kb = U.lo; kb < U.hi; kb += NS) {
+      const int cnt = min(NS, U.hi - kb);
+      bool run_start = false;
+      if (lane < cnt) {
+        const int2 v = a.visits[kb + lane];
+        run_start = (v.y >> 12) & 1;
+        const float* ps = a.psi + (size_t)v.x * 3 * W;
+        {
+          float t[W];
+          load_taps<float, W>(ps, t);
+#pragma unroll
+          for (int k = 0; k < W; ++k) st->px[lane][8 + k] = t[k];
+        }
+        const int sy = v.y >> 13;
+        {
+          float t[W];
+          load_taps<float, W>(ps + W, t);
+          float2* pyr = reinterpret_cast<float2*>(st->py[lane]);
+          const int rot = sy % W;  // tap dy feeds row s + dy, held in register (s + dy) mod W
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            const int q = rot + k < W ? rot + k : rot + k - W;
+            pyr[q] = make_float2(t[k], t[k]);
+          }
+        }
+        const float2 cq = __ldg(a.c + v.x);
+        const int ox = (v.y & 63) - 16;
+        const unsigned pxo = st_off + (unsigned)(offsetof(S, px) + (lane * S::PX + 8 - ox) * sizeof(float));
+        st->hd[lane] = make_int4((int)pxo, 0, __float_as_int(cq.x), __float_as_int(cq.y));
+        st->sz[lane] = sy;
+      }
+      // runs of one first y tap (bit j set where staged visit j starts one; visit 0 always
+      // starts the batch's first run)
+      unsigned starts = __ballot_sync(0xffffffffu, run_start) | 1u;
+      __syncwarp();
+      while (starts) {
+        const int j0 = __ffs(starts) - 1;
+        starts &= starts - 1;
+        const int j1 = starts ? __ffs(starts) - 1 : cnt;
+        const int sr = st->sz[j0];
+        while (zb < sr) flush();
+        for (int j = j0 + g; j < j1; j += 4) {
+          const int4 h = st->hd[j];
+          const float wx = *reinterpret_cast<const float*>(smem_raw + h.x + lx4);
+          const float2 cw = make_float2(wx * __int_as_float(h.z), wx * __int_as_float(h.w));
+          const float4* p4 = reinterpret_cast<const float4*>(st->py[j]);
+#pragma unroll
+          for (int k = 0; k < W / 2; ++k) {
+            const float4 q = p4[k];
+            acc[2 * k] = __ffma2_rn(cw, make_float2(q.x, q.y), acc[2 * k]);
+            acc[2 * k + 1] = __ffma2_rn(cw, make_float2(q.z, q.w), acc[2 * k + 1]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    while (zb < U.z1) flush();
+  }
+}
+
+// 2D rows that several column units touch: eight lanes per entry (one per cell), the entry's
+// partial slots summed in slot order (deterministic), eight loads in flight at a time.
+__global__ void __launch_bounds__(256)
+    k_reduce_col2(const ColRed* __restrict__ red, int nred, const float2* __restrict__ partial,
+                  float2* __restrict__ fine, int nfx) {
+  const int e = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 3);
+  if (e >= nred) return;
+  const int lx = threadIdx.x & 7;
+  const int4 r = __ldg(reinterpret_cast<const int4*>(red) + e);  // col, row, s0, ns
+  const float2* src = partial + (size_t)r.z * kColX + lx;
+  float2 sum = make_float2(0.f, 0.f);
+  int k = 0;
+  for (; k + 8 <= r.w; k += 8) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldcs(src + (size_t)(k + q) * kColX);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sum.x += v[q].x;
+      sum.y += v[q].y;
+    }
+  }
+  for (; k < r.w; ++k) {
+    const float2 v = __ldcs(src + (size_t)k * kColX);
+    sum.x += v.x;
+    sum.y += v.y;
+  }
+  fine[(long long)r.y * nfx + r.x * kColX + lx] = sum;
+}
+
+// the column spread kernel of a plan's dimension, and its per-CTA shared memory
+template <int W, int NS, bool COMP, int DIM>
+struct ColKernel {
+  static void (*fn())(ColArgs) { return k_spread_col<W, NS, COMP>; }
+  static constexpr size_t smem = sizeof(ColStage<W, NS>) * (kColThreads / 32);
+};
+template <int W, int NS>
+struct ColKernel<W, NS, false, 2> {
+  static void (*fn())(ColArgs) { return k_spread_col2<W, NS>; }
+  static constexpr size_t smem = sizeof(ColStage2<W, NS>) * (kColThreads / 32);
+};
+
+template <int W, int NS, bool COMP, int DIM>
 int configure_spread_col(Plan& p) {
-  const size_t smem = sizeof(ColStage<W, NS>) * (kColThreads / 32);
-  auto kern = k_spread_col<W, NS, COMP>;
+  const size_t smem = ColKernel<W, NS, COMP, DIM>::smem;
+  auto kern = ColKernel<W, NS, COMP, DIM>::fn();
   {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -665,7 +839,7 @@ int configure_spread_col(Plan& p) {
   return DDI_OK;
 }
 
-template <int W, int NS, bool COMP>
+template <int W, int NS, bool COMP, int DIM>
 int launch_spread_col(Plan& p, cudaStream_t s) {
   ColArgs a;
   for (int d = 0; d < 3; ++d) a.nf[d] = p.nf[d];
@@ -680,12 +854,17 @@ int launch_spread_col(Plan& p, cudaStream_t s) {
   a.partial = static_cast<float2*>(p.d_cpart);
   a.unit_slots = p.d_cslots;
   DDI_CUDA(cudaMemsetAsync(p.d_counter, 0, sizeof(int), s));
-  k_spread_col<W, NS, COMP><<<p.spread_blocks, kColThreads, p.spread_smem, s>>>(a);
+  ColKernel<W, NS, COMP, DIM>::fn()<<<p.spread_blocks, kColThreads, p.spread_smem, s>>>(a);
   DDI_LAUNCH_CHECK();
   p.mark("spread", s);
   if (p.ncred > 0) {
-    k_reduce_col<<<(unsigned)((p.ncred + 7) / 8), 256, 0, s>>>(p.d_cred, p.ncred, static_cast<const float2*>(p.d_cpart),
-                                                               static_cast<float2*>(p.d_fine), p.nf[0], p.nf[1], a.ncx);
+    if (DIM == 3)
+      k_reduce_col<<<(unsigned)((p.ncred + 7) / 8), 256, 0, s>>>(
+          p.d_cred, p.ncred, static_cast<const float2*>(p.d_cpart), static_cast<float2*>(p.d_fine), p.nf[0], p.nf[1],
+          a.ncx);
+    else
+      k_reduce_col2<<<(unsigned)((p.ncred + 31) / 32), 256, 0, s>>>(
+          p.d_cred, p.ncred, static_cast<const float2*>(p.d_cpart), static_cast<float2*>(p.d_fine), p.nf[0]);
     DDI_LAUNCH_CHECK();
     p.mark("spread_reduce", s);
   }
@@ -694,8 +873,10 @@ int launch_spread_col(Plan& p, cudaStream_t s) {
 
 template <int W>
 int spread_col_ns(Plan& p, cudaStream_t s, bool configure) {
-  if (p.col_comp) return configure ? configure_spread_col<W, 32, true>(p) : launch_spread_col<W, 32, true>(p, s);
-  return configure ? configure_spread_col<W, 32, false>(p) : launch_spread_col<W, 32, false>(p, s);
+  if (p.dim == 2)  // 2D columns carry no compensated variant (such plans take the tile spread)
+    return configure ? configure_spread_col<W, 32, false, 2>(p) : launch_spread_col<W, 32, false, 2>(p, s);
+  if (p.col_comp) return configure ? configure_spread_col<W, 32, true, 3>(p) : launch_spread_col<W, 32, true, 3>(p, s);
+  return configure ? configure_spread_col<W, 32, false, 3>(p) : launch_spread_col<W, 32, false, 3>(p, s);
 }
 
 int spread_col_w(Plan& p, cudaStream_t s, bool configure) {

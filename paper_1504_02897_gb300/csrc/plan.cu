@@ -220,7 +220,9 @@ int build_spread(Plan& p, cudaStream_t stream) {
   }
   p.pairs = pairs;
   // long units are cut into pieces that write partial planes (summed by k_reduce)
-  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(1024, pairs / (152LL * 32 * 2));
+  // (at least 1024 visits in 3D, 256 in 2D: a hot 2D tile's pieces run one after another
+  // on one warp each, so shorter pieces shorten the launch's critical path)
+  p.chunk = d.chunk > 0 ? d.chunk : (int)std::max<long long>(dim == 2 ? 256 : 1024, pairs / (152LL * 32 * 2));
   std::vector<SpreadUnit> work;
   std::vector<SplitUnit> split;
   int slot = 0;
@@ -254,25 +256,44 @@ int build_spread(Plan& p, cudaStream_t stream) {
   return configure_kernels(p);
 }
 
-// Whether the column spread applies: FP32 3D plans whose fine grid holds whole columns and
-// is wide enough that a footprint meets a column (or a z-window) in one contiguous piece.
+// Whether the column spread applies: FP32 plans whose fine grid holds whole columns and is
+// wide enough that a footprint meets a column (or a window) in one contiguous piece.  2D
+// columns carry no compensated variant (compensated 2D plans use the tile spread).
 bool columns_apply(const Plan& p) {
-  return p.dim == 3 && p.prec == DDI_FP32 && p.nf[0] % kColX == 0 && p.nf[1] % kColY == 0 &&
-         p.nf[0] >= kColX + p.w - 1 && p.nf[1] >= kColY + p.w - 1 && p.nf[2] >= p.w && p.w <= 16;
+  if (p.prec != DDI_FP32 || p.w > 16 || p.nf[0] % kColX != 0 || p.nf[0] < kColX + p.w - 1) return false;
+  if (p.dim == 2) return p.nf[1] >= p.w && p.desc.compensated == 0;
+  return p.dim == 3 && p.nf[1] % kColY == 0 && p.nf[1] >= kColY + p.w - 1 && p.nf[2] >= p.w;
 }
 
-// Column spread lists.  Every processed node visits the columns its x-y taps reach; a
-// column's visits are sorted by the node's first z tap (then by node).  The visits are cut
-// into units of at most `chunk` visits; unit c writes the planes [a_c, e_c), a_c = its first
-// visit's first tap, e_c the end of its last footprint extended over the gap to the next
-// unit (at most 64 planes ahead; longer gaps and empty columns get units without visits that
-// only write zeros).  A plane that several units touch (their footprints overlap at unit
+// Frees the spread lists of both schemes (the autotuner switches a 2D plan between them).
+void drop_spread_lists(Plan& p) {
+  for (void** q : {(void**)&p.d_visits, (void**)&p.d_units, (void**)&p.d_split, &p.d_partial, (void**)&p.d_cvis,
+                   (void**)&p.d_cunits, (void**)&p.d_cred, (void**)&p.d_cslots, &p.d_cpart})
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+  p.bytes -= p.spread_bytes;
+  p.spread_bytes = 0;
+}
+
+// Column spread lists.  3D: columns of kColX x kColY cells in x-y run the whole z axis (the
+// window axis); 2D: columns of kColX cells in x run the whole y axis.  Every processed node
+// visits the columns its cross-axis taps reach; a column's visits are sorted by the node's
+// first tap along the window axis, then (3D) by z class, then by node.  The visits are cut
+// into units of at most `chunk` visits; unit c writes the planes (2D: rows) [a_c, e_c), a_c =
+// its first visit's first tap, e_c the end of its last footprint extended over the gap to the
+// next unit (at most 64 planes ahead; longer gaps and empty columns get units without visits
+// that only write zeros).  A plane that several units touch (their footprints overlap at unit
 // boundaries, and the last unit of a column wraps onto the first) is a leading or trailing
 // plane of each of them: those go to partial slots and a reduce entry sums them in unit order;
 // every other plane is written by its one unit.  Every fine cell is written once per apply.
 int build_spread_col(Plan& p, cudaStream_t stream) {
-  const int W = p.w, nfx = p.nf[0], nfy = p.nf[1], nfz = p.nf[2];
-  const int ncx = nfx / kColX, ncy = nfy / kColY, ncol = ncx * ncy;
+  const bool d3 = p.dim == 3;
+  const int W = p.w, nfx = p.nf[0], nfy = p.nf[1];
+  const int nfz = p.nf[p.dim - 1];  // the window axis: z (3D), y (2D)
+  const int cy_cells = d3 ? kColY : 1;
+  const int ncx = nfx / kColX, ncy = d3 ? nfy / kColY : 1, ncol = ncx * ncy;
   DDI_CUDA(cudaStreamSynchronize(stream));
   for (void** q : {(void**)&p.d_cvis, (void**)&p.d_cunits, (void**)&p.d_cred, (void**)&p.d_cslots, &p.d_cpart})
     if (*q) {
@@ -281,7 +302,7 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
     }
   p.bytes -= p.spread_bytes;
   const size_t before = p.bytes;
-  // visits: key (column, first z tap) and the packed entry
+  // visits: key (column, first window-axis tap) and the packed entry
   auto span = [&](int l, int nf, int B, int* first) {  // blocks of B cells a footprint from l reaches
     *first = l / B;
     const int last = ((l + W - 1) % nf) / B;
@@ -289,10 +310,16 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
     if (k < 0) k += nf / B;
     return k + 1;
   };
+  auto yspan = [&](int l, int* first) {  // 2D: the one column row
+    if (d3) return span(l, nfy, kColY, first);
+    *first = 0;
+    return 1;
+  };
+  auto wtap = [&](const ushort4& l) { return d3 ? (int)l.z : (int)l.y; };
   std::vector<int> count(ncol + 1, 0);
   for (int64_t i = 0; i < p.Mh; ++i) {
     int fx, fy;
-    const int kx = span(p.h_l0[i].x, nfx, kColX, &fx), ky = span(p.h_l0[i].y, nfy, kColY, &fy);
+    const int kx = span(p.h_l0[i].x, nfx, kColX, &fx), ky = yspan(p.h_l0[i].y, &fy);
     for (int b = 0; b < ky; ++b)
       for (int a = 0; a < kx; ++a) ++count[((fy + b) % ncy) * ncx + (fx + a) % ncx];
   }
@@ -309,22 +336,22 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
     for (int64_t i = 0; i < p.Mh; ++i) {
       const ushort4 l = p.h_l0[i];
       int fx, fy;
-      const int kx = span(l.x, nfx, kColX, &fx), ky = span(l.y, nfy, kColY, &fy);
+      const int kx = span(l.x, nfx, kColX, &fx), ky = yspan(l.y, &fy);
       for (int b = 0; b < ky; ++b)
         for (int a = 0; a < kx; ++a) {
           const int bx = (fx + a) % ncx, by = (fy + b) % ncy;
-          const int ox = rel_start(l.x, bx * kColX, nfx, W), oy = rel_start(l.y, by * kColY, nfy, W);
-          if (ox < -(W - 1) || ox >= kColX || oy < -(W - 1) || oy >= kColY) {
+          const int ox = rel_start(l.x, bx * kColX, nfx, W), oy = d3 ? rel_start(l.y, by * kColY, nfy, W) : 0;
+          if (ox < -(W - 1) || ox >= kColX || oy < -(W - 1) || oy >= cy_cells) {
             set_error("column spread: footprint offset (%d, %d) outside its column", ox, oy);
             return DDI_ERR_INTERNAL;
           }
-          vis[fill[by * ncx + bx]++] = make_int2((int)i, ((int)l.z << 13) | ((oy + 16) << 6) | (ox + 16));
+          vis[fill[by * ncx + bx]++] = make_int2((int)i, (wtap(l) << 13) | ((oy + 16) << 6) | (ox + 16));
         }
     }
   }
-  // per column: by first z tap, then z class (nodes with the same first tap and bit-identical
-  // psi_z rows, e.g. one quadrature ring), then node (the visits are in node order already);
-  // bit 12 marks the first visit of each run of one z class
+  // per column: by first window-axis tap, then z class (3D: nodes with the same first tap and
+  // bit-identical psi_z rows, e.g. one quadrature ring; 2D: one class), then node (the visits
+  // are in node order already); bit 12 marks the first visit of each run of one (tap, class)
   for (int c = 0; c < ncol; ++c) {
     auto b = vis.begin() + start[c], e = vis.begin() + start[c + 1];
     std::stable_sort(b, e, [&](const int2& u, const int2& v) {
@@ -332,7 +359,8 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
       return su != sv ? su < sv : p.h_zcls[u.x] < p.h_zcls[v.x];
     });
     for (auto it = b; it != e; ++it)
-      if (it == b || p.h_zcls[it->x] != p.h_zcls[(it - 1)->x]) it->y |= 1 << 12;
+      if (it == b || (it->y >> 13) != ((it - 1)->y >> 13) || p.h_zcls[it->x] != p.h_zcls[(it - 1)->x])
+        it->y |= 1 << 12;
   }
   const int cap = p.desc.chunk > 0 ? p.desc.chunk : 256;
   const int lmax = std::min(64, nfz);
@@ -348,8 +376,8 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
     if (b0 == b1) {
       // an empty column is written as zeros, unless none of its x or y lines holds a tap (the
       // NUFFT's passes neither transform nor read those lines)
-      bool in_y = false, in_x = false;
-      for (int r = 0; r < kColY; ++r) {
+      bool in_y = !d3, in_x = false;  // a 2D column holds every y line
+      for (int r = 0; d3 && r < kColY; ++r) {
         int d = (c / ncx) * kColY + r - p.yr[0];
         if (d < 0) d += nfy;
         in_y = in_y || d < p.yr[1];
@@ -411,10 +439,41 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
       contrib[z].clear();
     }
   }
-  // costliest units first (visits, and the planes each writes)
-  std::stable_sort(units.begin(), units.end(), [](const ColUnit& a, const ColUnit& b) {
-    return (a.hi - a.lo) + (a.z1 - a.z0) > (b.hi - b.lo) + (b.z1 - b.z0);
-  });
+  // costliest units first.  3D: visits plus the planes each writes.  2D: the four lane
+  // groups share a run (one first y tap), so a run of L visits takes ceil(L / 4) steps; a
+  // unit costs about 4 per step, 3 per run and 5 per row it writes (relative instruction
+  // counts of the kernel's visit step, run start and row flush)
+  {
+    std::vector<long long> cost(units.size());
+    for (size_t u = 0; u < units.size(); ++u) {
+      const ColUnit& U = units[u];
+      if (d3) {
+        cost[u] = (long long)(U.hi - U.lo) + (U.z1 - U.z0);
+        continue;
+      }
+      long long steps = 0, runs = 0;
+      int len = 0;
+      for (int k = U.lo; k < U.hi; ++k) {
+        if (k > U.lo && ((vis[k].y >> 12) & 1)) {
+          steps += (len + 3) / 4;
+          ++runs;
+          len = 0;
+        }
+        ++len;
+      }
+      if (len > 0) {
+        steps += (len + 3) / 4;
+        ++runs;
+      }
+      cost[u] = 4 * steps + 3 * runs + 5LL * (U.z1 - U.z0);
+    }
+    std::vector<size_t> ord(units.size());
+    std::iota(ord.begin(), ord.end(), (size_t)0);
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<ColUnit> sorted(units.size());
+    for (size_t k = 0; k < ord.size(); ++k) sorted[k] = units[ord[k]];
+    units.swap(sorted);
+  }
   if (units.size() > (size_t)INT32_MAX || slots.size() > (size_t)INT32_MAX) {
     set_error("column spread: work list too long");
     return DDI_ERR_ARG;
@@ -429,13 +488,14 @@ int build_spread_col(Plan& p, cudaStream_t stream) {
   DDI_TRY(upload(p, (void**)&p.d_cunits, units, "column units", stream));
   DDI_TRY(upload(p, (void**)&p.d_cred, red, "column reduce entries", stream));
   DDI_TRY(upload(p, (void**)&p.d_cslots, slots, "column slot lists", stream));
-  DDI_TRY(dev_alloc(p, &p.d_cpart, p.cx_size() * kColX * kColY * (size_t)std::max(1, nslot), "column partial planes"));
+  DDI_TRY(dev_alloc(p, &p.d_cpart, p.cx_size() * kColX * cy_cells * (size_t)std::max(1, nslot),
+                    "column partial planes"));
   p.spread_bytes = p.bytes - before;
   DDI_CUDA(cudaStreamSynchronize(stream));
   return configure_kernels(p);
 }
 
-int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool gpe) {
+int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool gpe, bool batch_item) {
   std::string err;
   {
     const int st = normalise_desc(desc_in, &p.desc, &err);
@@ -465,12 +525,24 @@ int create_plan(Plan& p, const ddi_plan_desc* desc_in, cudaStream_t stream, bool
   choose_tile(p);
   const int dim = d.dim, W = p.w;
   if (d.spread == DDI_SPREAD_COLUMNS && !columns_apply(p)) {
-    set_error("the column spread needs an FP32 3D plan whose fine grid is a multiple of %d x %d in x-y and at "
-              "least w + %d, w + %d and w cells along x, y and z",
-              kColX, kColY, kColX - 1, kColY - 1);
+    set_error("the column spread needs an FP32 plan whose fine grid is a multiple of %d cells in x (3D: %d x %d in "
+              "x-y) and at least w + %d cells along x (3D: w + %d along y and w along z; 2D: w along y), and no "
+              "compensated arithmetic in 2D",
+              kColX, kColX, kColY, kColX - 1, kColY - 1);
     return DDI_ERR_ARG;
   }
-  p.spread_kind = (d.spread != DDI_SPREAD_TILES && columns_apply(p)) ? DDI_SPREAD_COLUMNS : DDI_SPREAD_TILES;
+  // automatic choice: columns in 3D.  In 2D, a plan on its own takes columns only up to 512^2
+  // fine cells; above that the tile spread measured faster alone (the 2D column's runs of one
+  // first y tap are short there, so three of its four lane groups idle), and its autotuner
+  // times both schemes.  Batch items take columns at every size: they run beside the other
+  // items' kernels, and the 96-density batch measured 13.3 ms with columns against 15.5 ms
+  // with tiles (the faster tiles alone) and 15.2 ms with the size rule
+  p.batch_item = batch_item;
+  p.spread_kind = columns_apply(p) && (d.spread == DDI_SPREAD_COLUMNS ||
+                                       (d.spread == DDI_SPREAD_AUTO &&
+                                        (p.dim == 3 || batch_item || (long long)p.nf[0] * p.nf[1] <= 512LL * 512)))
+                      ? DDI_SPREAD_COLUMNS
+                      : DDI_SPREAD_TILES;
   // compensated FP32 arithmetic: head + tail twiddles in the NUFFT's fine-grid passes and
   // compensated (Kahan) plane sums in the column spread
   p.precise_nufft = d.compensated != 0 && d.precision == DDI_FP32;
@@ -755,7 +827,7 @@ void fill_info(const Plan& p, ddi_plan_info* info) {
   info->yrange[1] = p.yr[1];
   if (p.spread_kind == DDI_SPREAD_COLUMNS) {
     info->tile[0] = kColX;
-    info->tile[1] = kColY;
+    info->tile[1] = p.dim == 3 ? kColY : p.nf[1];
     info->tile[2] = p.nf[2];
     info->spread_items = p.ncunits;
     info->spread_split_tiles = p.ncred;

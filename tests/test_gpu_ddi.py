@@ -128,13 +128,54 @@ def test_ddi_columns_small_fine_grids(D, n):
 
 
 def test_ddi_columns_rejected_where_they_do_not_apply(D):
-    # FP64 plans and 2D plans spread by tiles; asking for columns is an argument error
+    # FP64 plans spread by tiles, and so do compensated 2D plans (2D columns have no
+    # compensated variant); asking for columns there is an argument error
     with pytest.raises(D.DDIError):
         D.Plan(3, (16, 16, 16), (-1,) * 3, (2,) * 3, (0, 0, 1), precision=0, spread=2)
     with pytest.raises(D.DDIError):
-        D.Plan(2, (16, 16), (-1,) * 2, (2,) * 2, (0, 0, 1), precision=1, spread=2)
+        D.Plan(2, (16, 16), (-1,) * 2, (2,) * 2, (0, 0, 1), precision=1, spread=2, compensated=True)
     p = D.Plan(3, (16, 16, 16), (-1,) * 3, (2,) * 3, (0, 0, 1), precision=0)
     assert p.info.spread == 1
+    p = D.Plan(2, (16, 16), (-1,) * 2, (2,) * 2, (0, 0, 1), precision=1, compensated=True)
+    assert p.info.spread == 1
+    p = D.Plan(2, (16, 16), (-1,) * 2, (2,) * 2, (0, 0, 1), precision=1)
+    assert p.info.spread == 2 and tuple(p.info.tile[:2]) == (8, 32)
+
+
+def _rho_2d(n, lo, ln, seed):
+    rng = np.random.default_rng(seed)
+    X, Y = synth.coords(n, lo, ln)
+    return (np.exp(-((X - 0.4) ** 2 / 1.7 + (Y + 0.3) ** 2 / 0.9)) + 0.4 * np.exp(-((X + 1.5) ** 2 + (Y - 1) ** 2) / 0.6)) \
+        * (1 + 0.05 * rng.random(X.shape))
+
+
+@pytest.mark.parametrize("spread,chunk", [(1, 0), (2, 0), (2, 5), (2, 64), (2, 100000)])
+def test_ddi_2d_spread_schemes(D, spread, chunk):
+    # 2D FP32: tile spread and column spread (8-cell x columns, window along y) with the
+    # default units, tiny units (most rows shared by several units and summed by the reduce),
+    # and one unit per column (its window wraps onto itself)
+    n, lo, ln = (64, 48), (-8.0, -6.5), (16.0, 13.0)
+    axis = (np.sin(0.7), 0.0, np.cos(0.7))
+    rho = _rho_2d(n, lo, ln, 5)
+    plan = _plan(D, 2, n, lo, ln, axis, precision=1, spread=spread, chunk=chunk)
+    assert plan.info.spread == spread
+    got = _run(D, plan, rho)
+    ref = _oracle(_in(rho, 1), n, lo, ln, axis, dim=2)
+    assert _report(f"2d spread={spread} chunk={chunk}", 1, _relinf(got, ref)) <= TOL[1]
+
+
+@pytest.mark.parametrize("n", [(8, 8), (12, 8), (8, 24)])
+def test_ddi_2d_columns_small_fine_grids(D, n):
+    # the smallest 2D fine grids (16 cells: a footprint covers most of a column, windows
+    # wrap) and ragged ones, by the automatic choice (columns for FP32 2D plans)
+    lo = tuple(-0.25 * v for v in n)
+    ln = tuple(0.5 * v for v in n)
+    rho = _rho_2d(n, lo, ln, 9)
+    plan = _plan(D, 2, n, lo, ln, (0.6, 0.0, 0.8), precision=1)
+    assert plan.info.spread == 2
+    got = _run(D, plan, rho)
+    ref = _oracle(_in(rho, 1), n, lo, ln, (0.6, 0.0, 0.8), dim=2)
+    assert _report(f"2d columns n={n}", 1, _relinf(got, ref)) <= TOL[1]
 
 
 @pytest.mark.parametrize("precision", [0, 1])

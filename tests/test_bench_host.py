@@ -106,3 +106,14 @@ def test_split_side_run_reports_failure_instead_of_raising():
         pytest.skip("needs a machine without a GPU")
     res = bench.split_side_run(timeout_s=300)
     assert set(res) == {"error"} and res["error"]
+
+
+def test_side_run_reports_failure_instead_of_raising():
+    # the GPE and batch side runs fail without a GPU; the headline line then carries the reason
+    sys.path.insert(0, ROOT)
+    import torch
+    import bench
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU")
+    res = bench.side_run("tsfp128", timeout_s=300)
+    assert set(res) == {"error"} and res["error"]
